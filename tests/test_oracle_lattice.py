@@ -1,0 +1,128 @@
+"""Pins of the oracle's whole time step (collision + streaming, Eqs. 1 and 36)
+and of whole simulations against exact invariants, the viscosity of the
+Chapman-Enskog analysis, and the paper's own flat-interface results."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1412_5170_gb300 import synth
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+SCHEMES = [("bgk", "guo"), ("bgk", "edm"), ("bgk", "sc"), ("mrt", "guo")]
+
+
+@pytest.mark.parametrize("coll,forc", SCHEMES)
+def test_global_mass_and_momentum_are_conserved(orc, coll, forc):
+    """Collision conserves mass and adds F; sum_x F = 0 on a periodic lattice, and
+    streaming only moves populations: total mass and momentum stay constant."""
+    from oracle import coexistence as cx
+    rg, rl, _ = cx.maxwell(0.85)
+    nx, ny = 17, 15
+    rho0 = synth.density_field(nx, ny, "droplet", rl, rg, 5.0, seed=3, noise_amp=1e-4)
+    p = orc.params(nx, ny, 0.85, 1.0, -0.304, 1.0, coll, forc, s_e=0.8, s_eps=0.8, s_q=1.1)
+    f0 = orc.init_rest(rho0)
+    f, st = orc.run(p, f0, 300)
+    assert st == 0
+    m0 = f0.sum()
+    E = np.array([[0, 1, 0, -1, 0, 1, -1, -1, 1], [0, 0, 1, 0, -1, 1, 1, -1, -1]], float)
+    assert abs(f.sum() - m0) / m0 < 1e-13
+    mom = np.einsum("ayx,ia->i", f, E)
+    assert np.abs(mom).max() < 1e-13 * m0
+
+
+def test_streaming_moves_each_population_along_its_velocity(orc):
+    """Eq. 1 / Eq. 36: with tau = 1 and F = 0 (uniform rho) the collision returns
+    f^eq; a perturbation of population a at node x is found at x + e_a next step."""
+    nx, ny = 6, 5
+    rho = 0.2
+    f = orc.init_rest(np.full((ny, nx), rho))
+    p = orc.params(nx, ny, 0.7, 1.0, 0.0, 1.0)
+    g, st = orc.step(p, f)
+    np.testing.assert_allclose(g, f, atol=1e-17)
+    # BGK at tau -> large keeps most of the perturbation: check where it lands.
+    p = orc.params(nx, ny, 0.7, 1e6, 0.0, 1.0)
+    E = [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
+    for a, (ex, ey) in enumerate(E):
+        h = f.copy()
+        h[a, 2, 3] += 1e-3
+        out, _ = orc.step(p, h)
+        d = out - f
+        ya, xa = np.unravel_index(np.abs(d[a]).argmax(), d[a].shape)
+        assert (ya, xa) == ((2 + ey) % ny, (3 + ex) % nx)
+
+
+@pytest.mark.parametrize("coll", ["bgk", "mrt"])
+@pytest.mark.parametrize("tau", [0.6, 1.0, 1.4])
+def test_shear_wave_decays_at_the_lbgk_viscosity(orc, coll, tau):
+    """Sec. 3.2 after Eq. 25: nu = c_s^2 (tau - 1/2).  A single-phase shear wave
+    u_x = U sin(k y) (uniform rho, so F = 0) decays as exp(-nu k^2 t); the
+    lattice error is O(k^2)."""
+    ny, nx, U = 64, 1, 1e-4
+    k = 2 * np.pi / ny
+    rho = 0.25
+    f = np.zeros((9, ny, nx))
+    for y in range(ny):
+        f[:, y, 0] = orc.feq(rho, U * np.sin(k * (y + 0.5)), 0.0)
+    p = orc.params(nx, ny, 0.7, tau, -0.152, 1.0, coll, "guo", s_e=1.1, s_eps=1.2, s_q=1.3)
+
+    def amp(g):
+        m, _ = orc.macro(p, g)
+        return 2.0 / ny * np.sum(m["vx"][:, 0] * np.sin(k * (np.arange(ny) + 0.5)))
+
+    f, _ = orc.run(p, f, 40)
+    a1 = amp(f)
+    f, _ = orc.run(p, f, 400)
+    a2 = amp(f)
+    nu = -np.log(a2 / a1) / (k * k * 400)
+    assert nu == pytest.approx((tau - 0.5) / 3.0, rel=0.01)
+
+
+def _slab(orc, tr, A, K, tau, forcing="guo", coll="bgk", steps=15000, nx=4, ny=64):
+    from oracle import coexistence as cx
+    rg, rl, _ = cx.maxwell(tr, K)
+    rho0 = synth.density_field(nx, ny, "slab", rl, rg, ny / 4, seed=11)
+    p = orc.params(nx, ny, tr, tau, A, K, coll, forcing, s_e=0.8, s_eps=0.8, s_q=1.1)
+    f, st = orc.run(p, orc.init_rest(rho0), steps)
+    assert st == 0
+    m, _ = orc.macro(p, f)
+    return m["rho"][ny // 2].mean(), m["rho"][0].mean()
+
+
+@pytest.mark.parametrize("forcing", ["guo", "edm"])
+def test_flat_interface_is_tau_independent(orc, forcing):
+    """Sec. 4.2.1: for a straight interface the EDM and Guo coexistence densities
+    do not change with tau (Figs. 2-4); Shan-Chen's do."""
+    a = _slab(orc, 0.8, -0.26, 1.0, 0.7, forcing)
+    b = _slab(orc, 0.8, -0.26, 1.0, 1.5, forcing)
+    assert a[1] == pytest.approx(b[1], rel=1e-6)
+    assert a[0] == pytest.approx(b[0], rel=1e-7)
+
+
+def test_flat_interface_shan_chen_depends_on_tau(orc):
+    a = _slab(orc, 0.8, -0.26, 1.0, 0.8, "sc")
+    b = _slab(orc, 0.8, -0.26, 1.0, 1.5, "sc")
+    assert abs(a[1] - b[1]) / b[1] > 1e-2
+
+
+def test_guo_matches_mechanical_solution_better_than_edm(orc):
+    """Sec. 4.2.2 / Fig. 5: with eps = 0.52, A = -0.26, K = 1 the Guo gas density
+    follows the mechanical solution (Eq. 18) much better than EDM's."""
+    from oracle import coexistence as cx
+    mech_g, mech_l, _ = cx.mechanical(0.8, 1.0, 0.52)
+    guo = _slab(orc, 0.8, -0.26, 1.0, 1.0, "guo")
+    edm = _slab(orc, 0.8, -0.26, 1.0, 1.0, "edm")
+    assert guo[1] == pytest.approx(mech_g, rel=0.02)
+    assert guo[0] == pytest.approx(mech_l, rel=0.002)
+    assert abs(edm[1] - mech_g) > 10 * abs(guo[1] - mech_g)
+
+
+@pytest.mark.parametrize("K,A,key,rel", [(0.1, -1.0, "simulation_K0.1_eps2_rho_g", 0.02),
+                                         (1.0, -0.84, "simulation_K1_eps1.68_rho_g", 0.05)])
+def test_table6_flat_interface_simulation(orc, K, A, key, rel):
+    """Table 6 (Sec. 4.4.1): simulated gas density of a flat interface at
+    T/Tc = 0.6 with (K = 0.1, eps = 2) and (K = 1, eps = 1.68), eps = -2A."""
+    rl, rg = _slab(orc, 0.6, A, K, 1.5, "guo", steps=20000, ny=128)
+    assert rg == pytest.approx(GOLD["table6"][key], rel=rel)
+    assert rl == pytest.approx(0.406, abs=2e-3)
