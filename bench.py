@@ -1,0 +1,312 @@
+"""Throughput benchmark of the fused D2Q9 pseudo-potential step on GB300.
+
+Workload (the paper's method at the throughput configuration): a 4096 x 4096
+periodic lattice holding a 16 x 16 array of droplets of radius 80 (one per
+256 x 256 cell), T/Tc = 0.7, tau = 0.8, MRT (s_e = s_eps = 0.8, s_q = 1.1)
+with Guo forcing, Kupershtokh weight A = -0.304 (A_K = -0.152 in
+Kupershtokh's own convention), K = 1; populations held in FP32 as deviations
+from w_a rho_v, FP64 reductions.  A "step" is one fused time step over the
+whole lattice; the timed region ends with the FP64 mass / max|v| reduction.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  N > 1 runs independent replicas, one per GPU
+(launched with torch.distributed.run); the value is the sum over replicas
+divided by the slowest replica's time.  --impl reference times the FP64 CPU
+oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SIDE = 4096
+CELL = 256
+RADIUS = 80.0
+T_OVER_TC, TAU, A_PAPER, K_EOS = 0.7, 0.8, -0.304, 1.0
+MRT = dict(s_e=0.8, s_eps=0.8, s_q=1.1)
+BYTES_PER_NODE = 72          # 9 FP32 deviations read + 9 written
+SEED = 20141217 + 2 * 1000
+
+# DRAM bytes (read + write) per launch of the strip kernel measured by ncu on
+# the workload above, keyed by the sha256 of the kernel sources it was taken
+# from; when the sources change the entry no longer matches and traffic is null.
+TRAFFIC_CAPTURES: dict = {}
+KERNEL_SOURCES = ["paper_1412_5170_gb300/csrc/lbm_strip.cu", "paper_1412_5170_gb300/csrc/lbm_device.cuh",
+                  "paper_1412_5170_gb300/csrc/lbm_kernels.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for s in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, s), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def workload_config(extra=None):
+    cfg = {"workload": "droplet array 4096x4096 (16x16 droplets, R=80), T/Tc=0.7, tau=0.8, MRT+Guo, "
+                       "A=-0.304 (A_K=-0.152), K=1, FP32-deviation populations, FP64 reductions",
+           "nx": N_SIDE, "ny": N_SIDE, "collision": "mrt", "forcing": "guo", "precision": "fp32_dev",
+           "l2": "inputs larger than L2 (2 x 604 MB population buffers vs 129 MB L2); no flush"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.out.close()
+
+    def summary(self):
+        if not self.proc or not self.path:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(value: float, ws: int, device=None) -> float:
+    """Max of a per-rank float over the job (identity for one rank)."""
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def initial_density(lbm, synth, seed):
+    rv, rl = lbm.maxwell(T_OVER_TC)
+    return synth.density_field(N_SIDE, N_SIDE, "droplet_array", rl, rv, RADIUS, seed=seed, cell=CELL), rv
+
+
+def cpu_oracle_rate(steps: int, side: int, seed: int):
+    """MLUPS of the FP64 CPU oracle, as it stands, on a side x side periodic
+    sample of the workload (one 256 x 256 droplet cell when side = 256)."""
+    import oracle
+    from oracle import coexistence as cx
+    from paper_1412_5170_gb300 import synth
+    rg, rl, _ = cx.maxwell(T_OVER_TC)
+    rho0 = synth.density_field(side, side, "droplet_array", rl, rg, RADIUS * side / CELL, seed=seed,
+                               cell=side)
+    q = oracle.params(side, side, T_OVER_TC, TAU, A_PAPER, K_EOS, "mrt", "guo", **MRT)
+    f = oracle.init_rest(rho0)
+    t0 = time.perf_counter()
+    _, st = oracle.run(q, f, steps)
+    el = time.perf_counter() - t0
+    return side * side * steps / el / 1e6, el
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    # Bounded per-step sample: one oracle step on a side x side periodic window,
+    # sized so warmup + steps stay within about two minutes on one host core.
+    total = args.steps + args.warmup
+    side = 256 if total * 65536 / 1.5e6 < 120 else (128 if total * 16384 / 1.5e6 < 120 else 64)
+    if args.warmup:
+        cpu_oracle_rate(args.warmup, side, SEED)
+    rate, el = cpu_oracle_rate(args.steps, side, SEED)
+    line = {"impl": "reference", "metric": "MLUPS", "value": rate, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": workload_config({"sample": "%dx%d periodic window per step" % (side, side)}),
+            "cpu_baseline": {"value": rate, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": "%d oracle steps on a %dx%d periodic window of the workload"
+                                       % (args.steps, side, side)},
+            "e2e": {"value": rate, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_setup()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_1412_5170_gb300 import lbm, synth
+
+    nodes = N_SIDE * N_SIDE
+    rho0, rv = initial_density(lbm, synth, SEED + rank)
+    p = lbm.make_params(N_SIDE, N_SIDE, T_OVER_TC, TAU, A_PAPER, K_EOS, "mrt", "guo", "fp32", rho_ref=rv, **MRT)
+    lat = lbm.Lattice(p)
+    stream = lat.stream
+    lat.init_density(rho0)
+    variant = lat.variant
+    for _ in range(args.warmup):
+        lat.step(1)
+    lat.stats()                      # also synchronises the stream
+    barrier(ws)
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier(ws)
+        ev[0].record(stream)
+        for _ in range(args.steps):
+            lat.step(1)
+        ev[1].record(stream)
+        st = lat.stats()            # FP64 reductions: observe + final reduce
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+    step_ms = ev[0].elapsed_time(ev[1])
+    total_ms = ev[0].elapsed_time(ev[2])
+    total_ms = max_over_ranks(total_ms, ws, dev)
+    kernel_ms = step_ms / max(args.steps, 1)
+    value = ws * nodes * args.steps / (total_ms * 1e-3) / 1e6
+
+    # End-to-end through the public API with host buffers: each e2e step is
+    # init from a pinned host density field, CHUNK fused steps, and a read of
+    # rho, vx, vy into pinned host buffers.
+    chunk = 100
+    e2e_steps = max(1, args.steps // chunk)
+    h_rho0 = torch.from_numpy(rho0).pin_memory().numpy()
+    h_out = [torch.empty((N_SIDE, N_SIDE), dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lat.init_density(h_rho0)
+        lat.step(chunk)
+        lat.read_moments(out=h_out)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws, dev)
+    e2e_value = ws * nodes * chunk * e2e_steps / e2e_s / 1e6
+
+    if rank == 0:
+        peak, peak_kind = measured_peaks()
+        achieved = BYTES_PER_NODE * nodes / (kernel_ms * 1e-3) / 1e9
+        traffic = TRAFFIC_CAPTURES.get(kernel_hash())
+        cpu_steps = args.cpu_steps
+        cpu_rate, cpu_el = cpu_oracle_rate(cpu_steps, CELL, SEED) if cpu_steps > 0 else (None, 0.0)
+        line = {
+            "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config({"parallelism": "replicas" if ws > 1 else "single",
+                                       "kernel_variant": "strip" if variant == 1 else "generic"}),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": "%s (hbm_gbs, copy)" % peak_kind,
+                         "kernel": "k_step_strip<float,float,MRT,GUO>", "kernel_ms": kernel_ms,
+                         "bytes_per_node": BYTES_PER_NODE},
+            "cpu_baseline": {"value": cpu_rate, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": "%d FP64 oracle steps on one 256x256 droplet cell (%.1f s)"
+                                       % (cpu_steps, cpu_el)},
+            "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": 8 * nodes,
+                    "d2h_bytes_per_step": 24 * nodes,
+                    "how": "lbm_init_density(pinned host rho0) + lbm_step(%d) + lbm_read_moments(pinned host) "
+                           "per e2e step, %d e2e steps" % (chunk, e2e_steps)},
+            "clocks": clk.summary(),
+            "gpu_launches": args.steps + 2,
+            "status": st["status"], "mass": st["mass"], "max_v": st["max_v"],
+        }
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=300,
+                    help="oracle steps on one 256x256 cell for cpu_baseline (0 = skip)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

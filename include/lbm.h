@@ -1,0 +1,194 @@
+/*
+ * lbm.h -- C ABI of liblbm, a GB300 (sm_103a) implementation of the
+ * single-component pseudo-potential D2Q9 lattice Boltzmann model analysed by
+ * Hu, Li & Uddin, "Force Method in a Pseudo-potential Lattice Boltzmann
+ * Model" (arXiv:1412.5170).
+ *
+ * One time step (Sec. 2, Eq. 1; Sec. 4.4.2, Eq. 36) on a periodic nx x ny
+ * lattice, fused into one kernel:
+ *   rho, u        Eq. 3 moments of the pulled populations
+ *   psi           Eq. 7 with G = -1 from the K-scaled Carnahan-Starling
+ *                 EOS, Eqs. 29-30 (a = 1, b = 4, R = 1): psi^2 = 2(rho/3 - p)
+ *   F             Kupershtokh's hybrid force, Eq. 6, weights w(1) = 1/3,
+ *                 w(2) = 1/12 (Eq. 4), U = G psi^2/2
+ *   v             u + F/(2 rho) (Sec. 3.2)
+ *   collision     BGK (Eq. 1) with Guo (Eq. 23), exact-difference (Eq. 22)
+ *                 or Shan-Chen velocity-shift (Eqs. 20-21) forcing, or MRT
+ *                 with Guo's source in moment space (Eqs. 34-35)
+ *   streaming     pull, periodic in x and y (Eq. 1 / Eq. 36)
+ *
+ * Conventions shared by every entry point:
+ *   - Lattice fields are row-major [ny][nx] (x fastest); populations are
+ *     [9][ny][nx] with the velocity order e0 = (0,0), e1..e4 = (1,0), (0,1),
+ *     (-1,0), (0,-1), e5..e8 = (1,1), (-1,1), (-1,-1), (1,-1).
+ *   - A is the weight of Eq. 6 exactly as printed there (eps = -2A,
+ *     Table 1).  T_over_Tc is the reduced temperature with Tc taken from the
+ *     constants of Eq. 29.
+ *   - Every function returns an int status (LBM_OK = 0 or an LBM_E_* code)
+ *     and never throws; lbm_strerror() names a status.  After an error the
+ *     context stays valid unless the error was LBM_E_CUDA.
+ *   - Pointers named *_host are host memory owned by the caller; pointers
+ *     named *_dev are device memory owned by the caller.  Memory the library
+ *     allocates it also frees (lbm_destroy / lbm_batch_destroy).
+ *   - Work is queued on the stream given at creation; calls that return
+ *     results in host memory synchronise that stream, others are
+ *     asynchronous.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define LBM_OK 0
+#define LBM_E_INVALID 1        /* bad argument (tau <= 1/2, T/Tc outside (0,1), K <= 0, size ...) */
+#define LBM_E_CUDA 2           /* a CUDA call failed; the context should be destroyed */
+#define LBM_E_NONFINITE 3      /* a population, density or velocity became NaN/Inf */
+#define LBM_E_EOS_DOMAIN 4     /* rho outside (0,1) or rho/3 - p < 0: psi undefined (Eq. 7) */
+#define LBM_E_TIMEOUT 5        /* a bounded device-side wait gave up */
+#define LBM_E_NOT_CONVERGED 6  /* run-to-steady reached max_steps */
+#define LBM_E_IO 7             /* checkpoint file could not be read or written / is corrupt */
+#define LBM_E_UNSUPPORTED 8    /* valid request this build does not support */
+
+typedef enum { LBM_BGK = 0, LBM_MRT = 1 } lbm_collision;            /* Eq. 1 / Eq. 34 */
+typedef enum { LBM_GUO = 0, LBM_EDM = 1, LBM_SC = 2 } lbm_forcing;   /* Eq. 23 / Eq. 22 / Eq. 21 */
+typedef enum { LBM_FP64 = 0, LBM_FP32_DEV = 1 } lbm_precision;
+typedef enum { LBM_SLAB = 0, LBM_DROPLET = 1, LBM_BUBBLE = 2, LBM_DROPLET_ARRAY = 3 } lbm_preset;
+
+/* Model and lattice parameters.
+ *   nx, ny        periodic lattice size, each >= 1 (nodes)
+ *   T_over_Tc     reduced temperature, 0 < T/Tc < 1 (Eq. 29)
+ *   tau           BGK relaxation time / MRT viscous time tau_nu, > 1/2
+ *   A             Eq. 6 weight (paper convention), any real
+ *   K             Eq. 30 EOS scale, > 0
+ *   s_e, s_eps, s_q   MRT rates of the e, eps and q moments (Eq. 35); the
+ *                 viscous rate is 1/tau and s_rho = s_j = 1 (they drop out
+ *                 under Guo forcing).  Ignored for BGK.
+ *   precision     LBM_FP64: populations and arithmetic in double.
+ *                 LBM_FP32_DEV: populations stored in float as deviations
+ *                 f_a - w_a rho_ref, arithmetic in float; reductions in double.
+ *   rho_ref       reference density of LBM_FP32_DEV (use the vapour density);
+ *                 ignored for LBM_FP64. */
+typedef struct {
+    int32_t nx, ny;
+    int32_t collision;   /* lbm_collision */
+    int32_t forcing;     /* lbm_forcing; MRT supports LBM_GUO only */
+    int32_t precision;   /* lbm_precision */
+    int32_t reserved;    /* must be 0 */
+    double T_over_Tc, tau, A, K;
+    double s_e, s_eps, s_q;
+    double rho_ref;
+} lbm_params;
+
+/* Whole-lattice observables at the current time t (FP64 reductions).
+ *   mass        sum of rho over the lattice
+ *   max_v       max |v|, v = u + F/(2 rho): the spurious-velocity magnitude Us_max
+ *   max_dv      max |v(t) - v(t_snap)| against the snapshot taken by the
+ *               previous lbm_stats(..., snapshot = 1) call; -1 if none
+ *   rho_min, rho_max   extremes of rho
+ *   rho_center  rho at node (nx/2, ny/2); rho_corner: rho at node (0, 0)
+ *   rho_row_mid mean of rho over row y = ny/2; rho_row0: over row y = 0
+ *   steps       time steps taken since the last initialisation
+ *   status      LBM_OK, or the first error code seen since the last check */
+typedef struct {
+    double mass, max_v, max_dv, rho_min, rho_max;
+    double rho_center, rho_corner, rho_row_mid, rho_row0;
+    int64_t steps;
+    int32_t status;
+    int32_t reserved;
+} lbm_stats_t;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* ---- library ---- */
+const char *lbm_strerror(int status);
+int lbm_version(void);   /* (major << 16) | minor */
+
+/* Critical temperature implied by Eq. 29's constants with a = 1, b = 4, R = 1. */
+double lbm_tc(void);
+
+/* Maxwell equal-area coexistence densities of the Eq. 29/30 EOS at T/Tc
+ * (Sec. 3.1, Eq. 19); K-independent (Sec. 4.1).  Host FP64.  Writes the
+ * vapour and liquid densities; LBM_E_INVALID if T/Tc is outside (0, 1). */
+int lbm_maxwell(double T_over_Tc, double *rho_v, double *rho_l);
+
+/* ---- single-lattice context ---- */
+
+/* Device bytes a context needs for p (populations x2, moment and snapshot
+ * buffers, reduction scratch).  Pass a block of at least this size to
+ * lbm_create to make the library use caller-owned device memory. */
+int lbm_workspace_bytes(const lbm_params *p, size_t *bytes);
+
+/* Create a context on the current CUDA device.
+ *   cuda_stream     cudaStream_t all work is queued on (NULL = default stream)
+ *   workspace_dev   NULL: the library allocates its device memory; else a
+ *                   caller-owned device block of workspace_bytes >= the value
+ *                   of lbm_workspace_bytes, 256-byte aligned, which must
+ *                   outlive the context
+ * The state is undefined until an lbm_init_* call. */
+int lbm_create(const lbm_params *p, void *cuda_stream, void *workspace_dev,
+               size_t workspace_bytes, lbm_ctx **out);
+void lbm_destroy(lbm_ctx *ctx);
+
+/* f_a(x, 0) = w_a rho0(x), the equilibrium at rest (initial condition; the
+ * paper does not state one).  rho0_host: ny*nx doubles. Resets the step count. */
+int lbm_init_density(lbm_ctx *ctx, const double *rho0_host);
+
+/* Same, from a density field already on the device (ny*nx doubles). */
+int lbm_init_density_dev(lbm_ctx *ctx, const double *rho0_dev);
+
+/* Built-in initial fields: rho0 = rho_v + (rho_l - rho_v) (1 - tanh(2 d/width))/2
+ * + noise_amp (2 xi - 1), xi = (SplitMix64(seed ^ (y nx + x)) >> 11) 2^-53, d the
+ * signed distance to the liquid (slab |y - ny/2| - size; droplet r - size
+ * about (nx/2, ny/2); bubble: phases swapped; droplet array: r - size about the
+ * centre of each cell of side 'cell').  rho_l, rho_v <= 0 select the Maxwell
+ * densities at the context's T/Tc. */
+int lbm_init_preset(lbm_ctx *ctx, int kind, double size, double width, double rho_l,
+                    double rho_v, int32_t cell, uint64_t seed, double noise_amp);
+
+/* Advance nsteps time steps (asynchronous).  Errors seen by the kernels
+ * (LBM_E_NONFINITE, LBM_E_EOS_DOMAIN) are latched and reported by
+ * lbm_stats / lbm_run_to_steady. */
+int lbm_step(lbm_ctx *ctx, int64_t nsteps);
+
+/* Observables at the current time (synchronises).  snapshot != 0 also stores
+ * v(t) for the next max_dv. */
+int lbm_stats(lbm_ctx *ctx, int snapshot, lbm_stats_t *out);
+
+/* Step until max|v(t) - v(t - check_every)| < tol, checking every
+ * check_every steps, or until max_steps.  steps_done (may be NULL) receives
+ * the steps taken by this call.  Returns LBM_OK when converged,
+ * LBM_E_NOT_CONVERGED at max_steps, or the latched kernel error. */
+int lbm_run_to_steady(lbm_ctx *ctx, double tol, int64_t check_every, int64_t max_steps,
+                      int64_t *steps_done);
+
+/* rho, vx, vy at the current time into caller host buffers of ny*nx doubles
+ * each (any may be NULL).  v = u + F/(2 rho).  Synchronises. */
+int lbm_read_moments(lbm_ctx *ctx, double *rho_host, double *vx_host, double *vy_host);
+
+/* Post-streaming populations f_a(x, t) (the distribution at the current time,
+ * before collision) as 9*ny*nx doubles, and the inverse.  Synchronises. */
+int lbm_read_populations(lbm_ctx *ctx, double *f_host);
+int lbm_write_populations(lbm_ctx *ctx, const double *f_host);
+
+/* Checkpoint: header (magic, version, params, steps), the raw population
+ * buffer and an FNV-1a checksum.  lbm_load needs a context created with the
+ * same params; it restores the state bit for bit. */
+int lbm_save(lbm_ctx *ctx, const char *path);
+int lbm_load(lbm_ctx *ctx, const char *path);
+
+/* Kernel variant in use: 0 = generic tiled kernel (any nx), 1 = pipelined
+ * strip kernel (nx % 4 == 0).  lbm_set_variant forces one (LBM_E_UNSUPPORTED
+ * if the lattice does not allow it); -1 restores the automatic choice. */
+int lbm_get_variant(lbm_ctx *ctx, int *variant);
+int lbm_set_variant(lbm_ctx *ctx, int variant);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

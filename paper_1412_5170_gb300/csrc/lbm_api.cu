@@ -1,0 +1,481 @@
+// lbm_api.cu -- the single-lattice context of the liblbm C ABI (include/lbm.h):
+// creation, initial conditions, stepping, observables, run-to-steady,
+// population I/O and checkpoints.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_host.h"
+#include "lbm_kernels.cuh"
+
+using namespace lbm;
+
+struct lbm_ctx {
+    lbm_params p;
+    cudaStream_t stream;
+    bool owns;              // workspace allocated by the library
+    void* ws;
+    size_t ws_bytes;
+    void* f[2];             // population buffers (T = double or float)
+    int cur;                // buffer holding the current state
+    double *rho, *vx, *vy;  // FP64 moment fields / staging
+    double2* vsnap;
+    bool have_snap;
+    Partial* parts;
+    int nparts;
+    DevStats* dstats;
+    unsigned* status;
+    DevStats* hstats;       // pinned host mirror
+    int64_t steps;
+    int variant_forced;     // -1 = automatic
+};
+
+namespace {
+
+inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+inline size_t tsize(const lbm_params& p) { return p.precision == LBM_FP64 ? sizeof(double) : sizeof(float); }
+
+dim3 generic_grid(const lbm_params& p)
+{
+    return dim3((p.nx + GTX - 1) / GTX, (p.ny + GTY - 1) / GTY);
+}
+
+struct Layout {
+    size_t f0, f1, rho, vx, vy, vsnap, parts, dstats, status, total;
+};
+
+Layout layout_of(const lbm_params& p)
+{
+    const size_t n = (size_t)p.nx * p.ny;
+    const dim3 g = generic_grid(p);
+    Layout L;
+    size_t o = 0;
+    L.f0 = o; o = align256(o + 9 * n * tsize(p));
+    L.f1 = o; o = align256(o + 9 * n * tsize(p));
+    L.rho = o; o = align256(o + n * sizeof(double));
+    L.vx = o; o = align256(o + n * sizeof(double));
+    L.vy = o; o = align256(o + n * sizeof(double));
+    L.vsnap = o; o = align256(o + n * sizeof(double2));
+    L.parts = o; o = align256(o + (size_t)g.x * g.y * sizeof(Partial));
+    L.dstats = o; o = align256(o + sizeof(DevStats));
+    L.status = o; o = align256(o + sizeof(unsigned));
+    L.total = o;
+    return L;
+}
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return LBM_OK;
+    std::fprintf(stderr, "liblbm: CUDA error %s\n", cudaGetErrorString(e));
+    return LBM_E_CUDA;
+}
+
+#define LBM_CUDA(call)                                 \
+    do {                                               \
+        int s_ = cuda_status(call);                    \
+        if (s_ != LBM_OK) return s_;                   \
+    } while (0)
+
+template <typename T, typename C, int COLL, int FORC>
+void launch_generic(lbm_ctx* c, const void* fin, void* fout)
+{
+    k_step_generic<T, C, COLL, FORC><<<generic_grid(c->p), GTX * GTY, 0, c->stream>>>(
+        (const T*)fin, (T*)fout, c->p.nx, c->p.ny, make_coef<C>(c->p), c->status);
+}
+
+template <typename T, typename C>
+void launch_generic_scheme(lbm_ctx* c, const void* fin, void* fout)
+{
+    const lbm_params& p = c->p;
+    if (p.collision == LBM_MRT) launch_generic<T, C, MRT, GUO>(c, fin, fout);
+    else if (p.forcing == LBM_GUO) launch_generic<T, C, BGK, GUO>(c, fin, fout);
+    else if (p.forcing == LBM_EDM) launch_generic<T, C, BGK, EDM>(c, fin, fout);
+    else launch_generic<T, C, BGK, SC>(c, fin, fout);
+}
+
+int variant_of(const lbm_ctx* c)
+{
+    if (c->variant_forced >= 0) return c->variant_forced;
+    return lbm_strip_supported(&c->p) ? 1 : 0;
+}
+
+int step_once(lbm_ctx* c)
+{
+    const void* fin = c->f[c->cur];
+    void* fout = c->f[c->cur ^ 1];
+    if (variant_of(c) == 1) {
+        const int s = lbm_strip_launch(&c->p, fin, fout, c->status, c->stream);
+        if (s != LBM_OK) return s;
+    } else if (c->p.precision == LBM_FP64) {
+        launch_generic_scheme<double, double>(c, fin, fout);
+    } else {
+        launch_generic_scheme<float, float>(c, fin, fout);
+    }
+    LBM_CUDA(cudaGetLastError());
+    c->cur ^= 1;
+    c->steps += 1;
+    return LBM_OK;
+}
+
+template <typename T, typename C>
+void launch_observe(lbm_ctx* c, int mode)
+{
+    k_observe<T, C><<<generic_grid(c->p), GTX * GTY, 0, c->stream>>>(
+        (const T*)c->f[c->cur], c->p.nx, c->p.ny, make_coef<C>(c->p), mode, c->rho, c->vx, c->vy,
+        c->vsnap, c->parts, c->dstats, c->status);
+}
+
+int observe(lbm_ctx* c, int mode)
+{
+    if (c->p.precision == LBM_FP64) launch_observe<double, double>(c, mode);
+    else launch_observe<float, float>(c, mode);
+    LBM_CUDA(cudaGetLastError());
+    if (mode & OBS_REDUCE) {
+        k_reduce_final<<<1, 256, 0, c->stream>>>(c->parts, c->nparts, c->p.nx, c->dstats);
+        LBM_CUDA(cudaGetLastError());
+    }
+    return LBM_OK;
+}
+
+int status_code(unsigned bits)
+{
+    if (bits & ST_NONFINITE) return LBM_E_NONFINITE;
+    if (bits & ST_EOS) return LBM_E_EOS_DOMAIN;
+    if (bits & ST_TIMEOUT) return LBM_E_TIMEOUT;
+    return LBM_OK;
+}
+
+template <typename T>
+void launch_init_rest(lbm_ctx* c, const double* rho0)
+{
+    k_init_rest<T><<<1024, 256, 0, c->stream>>>(rho0, (T*)c->f[c->cur], c->p.nx, c->p.ny,
+                                                  c->p.precision == LBM_FP64 ? 0.0 : c->p.rho_ref);
+}
+
+template <typename T>
+void launch_plane(lbm_ctx* c, int a, int to_stored)
+{
+    k_plane_convert<T><<<1024, 256, 0, c->stream>>>((T*)c->f[c->cur], c->rho, a, c->p.nx, c->p.ny,
+                                                      c->p.precision == LBM_FP64 ? 0.0 : c->p.rho_ref,
+                                                      to_stored);
+}
+
+int reset_state(lbm_ctx* c)
+{
+    c->steps = 0;
+    c->have_snap = false;
+    LBM_CUDA(cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
+    return LBM_OK;
+}
+
+uint64_t fnv1a(const unsigned char* d, size_t n, uint64_t h = 1469598103934665603ull)
+{
+    for (size_t i = 0; i < n; ++i) { h ^= d[i]; h *= 1099511628211ull; }
+    return h;
+}
+
+const char kMagic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '1'};
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version, header_bytes;
+    lbm_params p;
+    int64_t steps;
+    uint64_t payload_bytes, checksum;
+};
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_strerror(int s)
+{
+    switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_E_INVALID: return "invalid argument";
+    case LBM_E_CUDA: return "CUDA error";
+    case LBM_E_NONFINITE: return "non-finite value in the lattice";
+    case LBM_E_EOS_DOMAIN: return "density outside the EOS domain (psi undefined)";
+    case LBM_E_TIMEOUT: return "device-side wait timed out";
+    case LBM_E_NOT_CONVERGED: return "not converged within max_steps";
+    case LBM_E_IO: return "checkpoint I/O error";
+    case LBM_E_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+    }
+}
+
+int lbm_version(void) { return (1 << 16) | 0; }
+
+int lbm_workspace_bytes(const lbm_params* p, size_t* bytes)
+{
+    if (!p || !bytes) return LBM_E_INVALID;
+    const int v = lbm_validate_params(p);
+    if (v != LBM_OK) return v;
+    *bytes = layout_of(*p).total;
+    return LBM_OK;
+}
+
+int lbm_create(const lbm_params* p, void* cuda_stream, void* workspace_dev, size_t workspace_bytes,
+               lbm_ctx** out)
+{
+    if (!p || !out) return LBM_E_INVALID;
+    *out = nullptr;
+    int v = lbm_validate_params(p);
+    if (v != LBM_OK) return v;
+    const Layout L = layout_of(*p);
+    if (workspace_dev && (workspace_bytes < L.total || ((uintptr_t)workspace_dev & 255))) return LBM_E_INVALID;
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return LBM_E_INVALID;
+    c->p = *p;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->owns = workspace_dev == nullptr;
+    c->ws_bytes = L.total;
+    if (c->owns) {
+        cudaError_t e = cudaMalloc(&c->ws, L.total);
+        if (e != cudaSuccess) { delete c; return cuda_status(e); }
+    } else {
+        c->ws = workspace_dev;
+    }
+    char* b = (char*)c->ws;
+    c->f[0] = b + L.f0;
+    c->f[1] = b + L.f1;
+    c->rho = (double*)(b + L.rho);
+    c->vx = (double*)(b + L.vx);
+    c->vy = (double*)(b + L.vy);
+    c->vsnap = (double2*)(b + L.vsnap);
+    c->parts = (Partial*)(b + L.parts);
+    const dim3 g = generic_grid(*p);
+    c->nparts = int(g.x * g.y);
+    c->dstats = (DevStats*)(b + L.dstats);
+    c->status = (unsigned*)(b + L.status);
+    c->cur = 0;
+    c->variant_forced = -1;
+    cudaError_t e = cudaMallocHost(&c->hstats, sizeof(DevStats));
+    if (e != cudaSuccess) {
+        if (c->owns) cudaFree(c->ws);
+        delete c;
+        return cuda_status(e);
+    }
+    if (cudaMemsetAsync(c->ws, 0, L.total, c->stream) != cudaSuccess) {
+        lbm_destroy(c);
+        return LBM_E_CUDA;
+    }
+    reset_state(c);
+    *out = c;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    if (c->owns && c->ws) cudaFree(c->ws);
+    if (c->hstats) cudaFreeHost(c->hstats);
+    delete c;
+}
+
+int lbm_init_density_dev(lbm_ctx* c, const double* rho0_dev)
+{
+    if (!c || !rho0_dev) return LBM_E_INVALID;
+    c->cur = 0;
+    if (c->p.precision == LBM_FP64) launch_init_rest<double>(c, rho0_dev);
+    else launch_init_rest<float>(c, rho0_dev);
+    LBM_CUDA(cudaGetLastError());
+    return reset_state(c);
+}
+
+int lbm_init_density(lbm_ctx* c, const double* rho0_host)
+{
+    if (!c || !rho0_host) return LBM_E_INVALID;
+    const size_t n = (size_t)c->p.nx * c->p.ny;
+    LBM_CUDA(cudaMemcpyAsync(c->rho, rho0_host, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    return lbm_init_density_dev(c, c->rho);
+}
+
+int lbm_init_preset(lbm_ctx* c, int kind, double size, double width, double rho_l, double rho_v,
+                    int32_t cell, uint64_t seed, double noise_amp)
+{
+    if (!c) return LBM_E_INVALID;
+    if (rho_l <= 0 || rho_v <= 0) {
+        const int s = lbm_maxwell(c->p.T_over_Tc, &rho_v, &rho_l);
+        if (s != LBM_OK) return s;
+    }
+    std::vector<double> rho0;
+    const int s = lbm_preset_field(c->p.nx, c->p.ny, kind, size, width, rho_l, rho_v, cell, seed,
+                                   noise_amp, rho0);
+    if (s != LBM_OK) return s;
+    const int r = lbm_init_density(c, rho0.data());
+    if (r != LBM_OK) return r;
+    LBM_CUDA(cudaStreamSynchronize(c->stream));   // rho0 is a local host vector
+    return LBM_OK;
+}
+
+int lbm_step(lbm_ctx* c, int64_t nsteps)
+{
+    if (!c || nsteps < 0) return LBM_E_INVALID;
+    for (int64_t i = 0; i < nsteps; ++i) {
+        const int s = step_once(c);
+        if (s != LBM_OK) return s;
+    }
+    return LBM_OK;
+}
+
+int lbm_stats(lbm_ctx* c, int snapshot, lbm_stats_t* out)
+{
+    if (!c || !out) return LBM_E_INVALID;
+    int mode = OBS_REDUCE;
+    if (c->have_snap) mode |= OBS_SNAP_CMP;
+    if (snapshot) mode |= OBS_SNAP_STORE;
+    int s = observe(c, mode);
+    if (s != LBM_OK) return s;
+    LBM_CUDA(cudaMemcpyAsync(c->hstats, c->dstats, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    const DevStats& d = *c->hstats;
+    out->mass = d.mass;
+    out->max_v = d.max_v;
+    out->max_dv = c->have_snap ? d.max_dv : -1.0;
+    out->rho_min = d.rho_min;
+    out->rho_max = d.rho_max;
+    out->rho_center = d.rho_center;
+    out->rho_corner = d.rho_corner;
+    out->rho_row_mid = d.rho_row_mid;
+    out->rho_row0 = d.rho_row0;
+    out->steps = c->steps;
+    out->status = status_code(d.status);
+    out->reserved = 0;
+    if (snapshot) c->have_snap = true;
+    return LBM_OK;
+}
+
+int lbm_run_to_steady(lbm_ctx* c, double tol, int64_t check_every, int64_t max_steps, int64_t* steps_done)
+{
+    if (!c || !(tol > 0) || check_every <= 0 || max_steps < 0) return LBM_E_INVALID;
+    int64_t done = 0;
+    if (steps_done) *steps_done = 0;
+    lbm_stats_t st;
+    int s = lbm_stats(c, 1, &st);
+    if (s != LBM_OK) return s;
+    if (st.status != LBM_OK) return st.status;
+    while (done < max_steps) {
+        const int64_t k = (max_steps - done < check_every) ? max_steps - done : check_every;
+        s = lbm_step(c, k);
+        if (s != LBM_OK) return s;
+        done += k;
+        if (steps_done) *steps_done = done;
+        s = lbm_stats(c, 1, &st);
+        if (s != LBM_OK) return s;
+        if (st.status != LBM_OK) return st.status;
+        if (k == check_every && st.max_dv >= 0 && st.max_dv < tol) return LBM_OK;
+    }
+    return LBM_E_NOT_CONVERGED;
+}
+
+int lbm_read_moments(lbm_ctx* c, double* rho_host, double* vx_host, double* vy_host)
+{
+    if (!c) return LBM_E_INVALID;
+    int s = observe(c, OBS_FIELDS);
+    if (s != LBM_OK) return s;
+    const size_t nb = (size_t)c->p.nx * c->p.ny * sizeof(double);
+    if (rho_host) LBM_CUDA(cudaMemcpyAsync(rho_host, c->rho, nb, cudaMemcpyDeviceToHost, c->stream));
+    if (vx_host) LBM_CUDA(cudaMemcpyAsync(vx_host, c->vx, nb, cudaMemcpyDeviceToHost, c->stream));
+    if (vy_host) LBM_CUDA(cudaMemcpyAsync(vy_host, c->vy, nb, cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_read_populations(lbm_ctx* c, double* f_host)
+{
+    if (!c || !f_host) return LBM_E_INVALID;
+    const size_t n = (size_t)c->p.nx * c->p.ny;
+    for (int a = 0; a < 9; ++a) {
+        if (c->p.precision == LBM_FP64) launch_plane<double>(c, a, 0);
+        else launch_plane<float>(c, a, 0);
+        LBM_CUDA(cudaGetLastError());
+        LBM_CUDA(cudaMemcpyAsync(f_host + a * n, c->rho, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    }
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_write_populations(lbm_ctx* c, const double* f_host)
+{
+    if (!c || !f_host) return LBM_E_INVALID;
+    const size_t n = (size_t)c->p.nx * c->p.ny;
+    c->cur = 0;
+    for (int a = 0; a < 9; ++a) {
+        LBM_CUDA(cudaMemcpyAsync(c->rho, f_host + a * n, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        if (c->p.precision == LBM_FP64) launch_plane<double>(c, a, 1);
+        else launch_plane<float>(c, a, 1);
+        LBM_CUDA(cudaGetLastError());
+    }
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    return reset_state(c);
+}
+
+int lbm_save(lbm_ctx* c, const char* path)
+{
+    if (!c || !path) return LBM_E_INVALID;
+    const size_t bytes = 9 * (size_t)c->p.nx * c->p.ny * tsize(c->p);
+    std::vector<unsigned char> buf(bytes);
+    LBM_CUDA(cudaMemcpyAsync(buf.data(), c->f[c->cur], bytes, cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    CkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kMagic, 8);
+    h.version = 1;
+    h.header_bytes = sizeof(CkptHeader);
+    h.p = c->p;
+    h.steps = c->steps;
+    h.payload_bytes = bytes;
+    h.checksum = fnv1a(buf.data(), bytes);
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return LBM_E_IO;
+    bool ok = std::fwrite(&h, sizeof(h), 1, fp) == 1 && std::fwrite(buf.data(), 1, bytes, fp) == bytes;
+    ok = (std::fclose(fp) == 0) && ok;
+    return ok ? LBM_OK : LBM_E_IO;
+}
+
+int lbm_load(lbm_ctx* c, const char* path)
+{
+    if (!c || !path) return LBM_E_INVALID;
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return LBM_E_IO;
+    CkptHeader h;
+    const size_t bytes = 9 * (size_t)c->p.nx * c->p.ny * tsize(c->p);
+    std::vector<unsigned char> buf(bytes);
+    bool ok = std::fread(&h, sizeof(h), 1, fp) == 1 && std::memcmp(h.magic, kMagic, 8) == 0 &&
+              h.version == 1 && h.header_bytes == sizeof(CkptHeader) &&
+              std::memcmp(&h.p, &c->p, sizeof(lbm_params)) == 0 && h.payload_bytes == bytes &&
+              std::fread(buf.data(), 1, bytes, fp) == bytes && fnv1a(buf.data(), bytes) == h.checksum;
+    std::fclose(fp);
+    if (!ok) return LBM_E_IO;
+    c->cur = 0;
+    LBM_CUDA(cudaMemcpyAsync(c->f[0], buf.data(), bytes, cudaMemcpyHostToDevice, c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    const int s = reset_state(c);
+    c->steps = h.steps;
+    return s;
+}
+
+int lbm_get_variant(lbm_ctx* c, int* variant)
+{
+    if (!c || !variant) return LBM_E_INVALID;
+    *variant = variant_of(c);
+    return LBM_OK;
+}
+
+int lbm_set_variant(lbm_ctx* c, int variant)
+{
+    if (!c || variant < -1 || variant > 1) return LBM_E_INVALID;
+    if (variant == 1 && !lbm_strip_supported(&c->p)) return LBM_E_UNSUPPORTED;
+    c->variant_forced = variant;
+    return LBM_OK;
+}
+
+}  // extern "C"

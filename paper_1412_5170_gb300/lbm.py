@@ -1,0 +1,223 @@
+"""Thin ctypes binding of liblbm (include/lbm.h), same names as the C ABI.
+
+Only argument marshalling happens here: every step of the lattice update runs
+in the CUDA kernels of ``liblbm.so``.  PyTorch supplies device memory (the
+context workspace) and the CUDA stream.  Importing this module fails if the
+library has not been built -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("liblbm.so is not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+OK, E_INVALID, E_CUDA, E_NONFINITE, E_EOS_DOMAIN, E_TIMEOUT, E_NOT_CONVERGED, E_IO, E_UNSUPPORTED = range(9)
+BGK, MRT = 0, 1
+GUO, EDM, SC = 0, 1, 2
+FP64, FP32_DEV = 0, 1
+SLAB, DROPLET, BUBBLE, DROPLET_ARRAY = 0, 1, 2, 3
+COLLISION = {"bgk": BGK, "mrt": MRT}
+FORCING = {"guo": GUO, "edm": EDM, "sc": SC}
+PRECISION = {"fp64": FP64, "fp32": FP32_DEV}
+PRESET = {"slab": SLAB, "droplet": DROPLET, "bubble": BUBBLE, "droplet_array": DROPLET_ARRAY}
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("collision", ctypes.c_int32),
+                ("forcing", ctypes.c_int32), ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("T_over_Tc", ctypes.c_double), ("tau", ctypes.c_double), ("A", ctypes.c_double),
+                ("K", ctypes.c_double), ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double),
+                ("s_q", ctypes.c_double), ("rho_ref", ctypes.c_double)]
+
+
+class lbm_stats_t(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("max_v", ctypes.c_double), ("max_dv", ctypes.c_double),
+                ("rho_min", ctypes.c_double), ("rho_max", ctypes.c_double), ("rho_center", ctypes.c_double),
+                ("rho_corner", ctypes.c_double), ("rho_row_mid", ctypes.c_double),
+                ("rho_row0", ctypes.c_double), ("steps", ctypes.c_int64), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+_vp, _dp, _i64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64
+_PROTOS = {
+    "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "lbm_version": (ctypes.c_int, []),
+    "lbm_tc": (ctypes.c_double, []),
+    "lbm_maxwell": (ctypes.c_int, [ctypes.c_double, _dp, _dp]),
+    "lbm_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(lbm_params), ctypes.POINTER(ctypes.c_size_t)]),
+    "lbm_create": (ctypes.c_int, [ctypes.POINTER(lbm_params), _vp, _vp, ctypes.c_size_t, ctypes.POINTER(_vp)]),
+    "lbm_destroy": (None, [_vp]),
+    "lbm_init_density": (ctypes.c_int, [_vp, _vp]),
+    "lbm_init_density_dev": (ctypes.c_int, [_vp, _vp]),
+    "lbm_init_preset": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double]),
+    "lbm_step": (ctypes.c_int, [_vp, _i64]),
+    "lbm_stats": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(lbm_stats_t)]),
+    "lbm_run_to_steady": (ctypes.c_int, [_vp, ctypes.c_double, _i64, _i64, ctypes.POINTER(_i64)]),
+    "lbm_read_moments": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lbm_read_populations": (ctypes.c_int, [_vp, _vp]),
+    "lbm_write_populations": (ctypes.c_int, [_vp, _vp]),
+    "lbm_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+    "lbm_load": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+    "lbm_get_variant": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "lbm_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
+}
+for _name, (_res, _args) in _PROTOS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+    globals()[_name] = _f
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (what, lbm_strerror(status).decode(), status))
+
+
+def check(status, what=""):
+    if status != OK:
+        raise LbmError(status, what)
+    return status
+
+
+def tc() -> float:
+    return lbm_tc()
+
+
+def maxwell(T_over_Tc: float):
+    """(rho_v, rho_l) of the Maxwell construction (Eq. 19), host FP64."""
+    rv, rl = ctypes.c_double(), ctypes.c_double()
+    check(lbm_maxwell(float(T_over_Tc), ctypes.byref(rv), ctypes.byref(rl)), "lbm_maxwell")
+    return rv.value, rl.value
+
+
+def make_params(nx, ny, T_over_Tc, tau, A, K=1.0, collision="bgk", forcing="guo", precision="fp64",
+                s_e=1.0, s_eps=1.0, s_q=1.0, rho_ref=None) -> lbm_params:
+    if rho_ref is None:
+        rho_ref = maxwell(T_over_Tc)[0] if precision == "fp32" else 0.0
+    return lbm_params(int(nx), int(ny), COLLISION[collision], FORCING[forcing], PRECISION[precision], 0,
+                      float(T_over_Tc), float(tau), float(A), float(K), float(s_e), float(s_eps), float(s_q),
+                      float(rho_ref))
+
+
+def _host_ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_vp)
+
+
+class Lattice:
+    """One periodic lattice on the current CUDA device.
+
+    The device workspace is a torch uint8 tensor and work runs on a torch
+    stream (its handle is passed to lbm_create); all arithmetic is in liblbm."""
+
+    def __init__(self, params: lbm_params, stream=None, torch_workspace: bool = True):
+        import torch
+        self.p = params
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        nbytes = ctypes.c_size_t()
+        check(lbm_workspace_bytes(ctypes.byref(params), ctypes.byref(nbytes)), "lbm_workspace_bytes")
+        self.workspace_bytes = nbytes.value
+        self._ws = None
+        ws_ptr = None
+        if torch_workspace:
+            self._ws = torch.empty(nbytes.value, dtype=torch.uint8, device="cuda")
+            ws_ptr = self._ws.data_ptr()
+        ctx = _vp()
+        check(lbm_create(ctypes.byref(params), _vp(self.stream.cuda_stream), _vp(ws_ptr) if ws_ptr else None,
+                         nbytes.value, ctypes.byref(ctx)), "lbm_create")
+        self.ctx = ctx
+
+    @property
+    def shape(self):
+        return (self.p.ny, self.p.nx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def init_density(self, rho0: np.ndarray):
+        rho0 = np.ascontiguousarray(rho0, dtype=np.float64)
+        assert rho0.shape == self.shape
+        check(lbm_init_density(self.ctx, _host_ptr(rho0)), "lbm_init_density")
+        self.stream.synchronize()   # rho0 is pageable host memory owned by this call
+
+    def init_density_dev(self, rho0_dev):
+        check(lbm_init_density_dev(self.ctx, _vp(rho0_dev.data_ptr())), "lbm_init_density_dev")
+
+    def init_preset(self, kind, size, width=4.0, rho_l=0.0, rho_v=0.0, cell=256, seed=0, noise_amp=1e-6):
+        check(lbm_init_preset(self.ctx, PRESET[kind] if isinstance(kind, str) else int(kind), float(size),
+                              float(width), float(rho_l), float(rho_v), int(cell), int(seed) & (2 ** 64 - 1),
+                              float(noise_amp)), "lbm_init_preset")
+
+    def step(self, n: int = 1):
+        check(lbm_step(self.ctx, int(n)), "lbm_step")
+
+    def stats(self, snapshot: bool = False) -> dict:
+        s = lbm_stats_t()
+        check(lbm_stats(self.ctx, int(bool(snapshot)), ctypes.byref(s)), "lbm_stats")
+        return s.as_dict()
+
+    def run_to_steady(self, tol, check_every=1000, max_steps=10 ** 6):
+        done = _i64()
+        st = lbm_run_to_steady(self.ctx, float(tol), int(check_every), int(max_steps), ctypes.byref(done))
+        return st, done.value
+
+    def read_moments(self, out=None):
+        """(rho, vx, vy) at the current time; out: three C-contiguous float64
+        arrays of the lattice shape to fill (e.g. pinned host memory)."""
+        rho, vx, vy = out if out is not None else (np.empty(self.shape) for _ in range(3))
+        check(lbm_read_moments(self.ctx, _host_ptr(rho), _host_ptr(vx), _host_ptr(vy)), "lbm_read_moments")
+        return rho, vx, vy
+
+    def read_populations(self) -> np.ndarray:
+        f = np.empty((9,) + self.shape)
+        check(lbm_read_populations(self.ctx, _host_ptr(f)), "lbm_read_populations")
+        return f
+
+    def write_populations(self, f: np.ndarray):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.shape == (9,) + self.shape
+        check(lbm_write_populations(self.ctx, _host_ptr(f)), "lbm_write_populations")
+
+    def save(self, path):
+        check(lbm_save(self.ctx, str(path).encode()), "lbm_save")
+
+    def load(self, path):
+        check(lbm_load(self.ctx, str(path).encode()), "lbm_load")
+
+    @property
+    def variant(self) -> int:
+        v = ctypes.c_int()
+        check(lbm_get_variant(self.ctx, ctypes.byref(v)), "lbm_get_variant")
+        return v.value
+
+    @variant.setter
+    def variant(self, v: int):
+        check(lbm_set_variant(self.ctx, int(v)), "lbm_set_variant")

@@ -1,0 +1,171 @@
+"""CUDA path (liblbm through its C ABI) against the FP64 CPU oracle, element by
+element, on seeded inputs.
+
+Tolerances:
+* FP64: max |f_gpu - f_oracle| / max |f| < 1e-12 (spec bar: max
+  |drho|/rho < 1e-12 after 1000 steps; reassociation and FMA contraction are
+  the only differences).
+* FP32 deviations: per-step rounding of float arithmetic on deviations
+  f - w rho_ref gives a relative density error of order 1e-7 per step that
+  the dissipative dynamics does not amplify; the element-wise bar after
+  200 steps is 2e-5 on rho, and the converged coexistence densities must
+  agree to 1e-4 relative with Us_max within 5 % (spec bars).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1412_5170_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+SCHEMES = [("bgk", "guo"), ("bgk", "edm"), ("bgk", "sc"), ("mrt", "guo")]
+MRT = dict(s_e=0.8, s_eps=0.8, s_q=1.1)
+
+
+def run_pair(lbm, nx, ny, steps, coll, forc, tr=0.8, tau=0.9, A=-0.304, K=1.0, precision="fp64",
+             kind="droplet", size=None, variant=None, seed=3):
+    rv, rl = lbm.maxwell(tr)
+    size = size if size is not None else max(2.0, min(nx, ny) / 4)
+    rho0 = synth.density_field(nx, ny, kind, rl, rv, size, seed=seed)
+    p = lbm.make_params(nx, ny, tr, tau, A, K, coll, forc, precision, **MRT)
+    with lbm.Lattice(p) as lat:
+        if variant is not None:
+            lat.variant = variant
+        lat.init_density(rho0)
+        lat.step(steps)
+        f_gpu = lat.read_populations()
+        st = lat.stats()
+    q = oracle.params(nx, ny, tr, tau, A, K, coll, forc, **MRT)
+    f_ref, ost = oracle.run(q, oracle.init_rest(rho0), steps)
+    return f_gpu, f_ref, st, ost
+
+
+@pytest.mark.parametrize("coll,forc", SCHEMES)
+@pytest.mark.parametrize("nx,ny", [(1, 7), (5, 3), (13, 11), (37, 29), (70, 9)])
+def test_generic_kernel_fp64_matches_oracle(lbm, nx, ny, coll, forc):
+    """Generic tiled kernel (any size; ragged tiles, lattices smaller than a tile)."""
+    f_gpu, f_ref, st, ost = run_pair(lbm, nx, ny, 60, coll, forc, variant=0, size=max(1.5, min(nx, ny) / 3))
+    assert st["status"] == 0 and ost == 0
+    assert np.abs(f_gpu - f_ref).max() / np.abs(f_ref).max() < 1e-12
+
+
+@pytest.mark.parametrize("coll,forc", SCHEMES)
+@pytest.mark.parametrize("nx,ny", [(4, 4), (8, 5), (12, 40), (260, 37), (512, 20)])
+def test_strip_kernel_fp64_matches_oracle(lbm, nx, ny, coll, forc):
+    """Pipelined strip kernel: single strip with both wraps, ragged last strip
+    (260 = 256 + 4), two full strips, chunks shorter than the stage ring."""
+    f_gpu, f_ref, st, ost = run_pair(lbm, nx, ny, 40, coll, forc, variant=1)
+    assert st["status"] == 0 and ost == 0
+    assert np.abs(f_gpu - f_ref).max() / np.abs(f_ref).max() < 1e-12
+
+
+def test_config1_fp64_1000_steps(lbm):
+    """64x64 flat slab, BGK + Guo, T/Tc = 0.8, tau = 1 (the plain-method case):
+    max |drho|/rho < 1e-12 after 1000 steps, default kernel."""
+    nx = ny = 64
+    rv, rl = lbm.maxwell(0.8)
+    rho0 = synth.density_field(nx, ny, "slab", rl, rv, 16, seed=20141217)
+    p = lbm.make_params(nx, ny, 0.8, 1.0, -0.304, 1.0, "bgk", "guo", "fp64")
+    with lbm.Lattice(p) as lat:
+        lat.init_density(rho0)
+        lat.step(1000)
+        rho, vx, vy = lat.read_moments()
+    q = oracle.params(nx, ny, 0.8, 1.0, -0.304, 1.0)
+    f_ref, _ = oracle.run(q, oracle.init_rest(rho0), 1000)
+    m, _ = oracle.macro(q, f_ref)
+    assert np.abs(rho - m["rho"]).max() / m["rho"].min() < 1e-12
+    assert np.abs(vx - m["vx"]).max() < 1e-13 and np.abs(vy - m["vy"]).max() < 1e-13
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("coll,forc", SCHEMES)
+def test_fp32_deviation_matches_oracle_elementwise(lbm, coll, forc, variant):
+    nx, ny, steps = 64, 48, 200
+    f_gpu, f_ref, st, ost = run_pair(lbm, nx, ny, steps, coll, forc, precision="fp32", variant=variant)
+    assert st["status"] == 0
+    rho_g, rho_r = f_gpu.sum(0), f_ref.sum(0)
+    assert np.abs(rho_g - rho_r).max() / rho_r.min() < 2e-5
+
+
+def test_strip_and_generic_agree(lbm):
+    for precision, tol in (("fp64", 1e-14), ("fp32", 1e-6)):
+        out = []
+        for v in (0, 1):
+            f, _, _, _ = run_pair(lbm, 96, 40, 30, "mrt", "guo", precision=precision, variant=v)
+            out.append(f)
+        assert np.abs(out[0] - out[1]).max() / np.abs(out[0]).max() < tol
+
+
+def test_fp32_coexistence_and_spurious_velocity(lbm):
+    """North-star FP32 bar on the 64x64 slab (BGK + Guo, T/Tc = 0.8): after
+    10000 steps the FP32-deviation coexistence densities agree with the FP64
+    oracle to 1e-4 relative and Us_max to 5 %."""
+    nx = ny = 64
+    steps = 10000
+    rv, rl = lbm.maxwell(0.8)
+    rho0 = synth.density_field(nx, ny, "slab", rl, rv, 16, seed=20141217)
+    p = lbm.make_params(nx, ny, 0.8, 1.0, -0.304, 1.0, "bgk", "guo", "fp32")
+    with lbm.Lattice(p) as lat:
+        lat.init_density(rho0)
+        lat.step(steps)
+        st = lat.stats()
+    q = oracle.params(nx, ny, 0.8, 1.0, -0.304, 1.0)
+    f_ref, _ = oracle.run(q, oracle.init_rest(rho0), steps)
+    m, _ = oracle.macro(q, f_ref)
+    rl_ref, rv_ref = m["rho"][ny // 2].mean(), m["rho"][0].mean()
+    us_ref = np.hypot(m["vx"], m["vy"]).max()
+    assert st["rho_row_mid"] == pytest.approx(rl_ref, rel=1e-4)
+    assert st["rho_row0"] == pytest.approx(rv_ref, rel=1e-4)
+    assert st["max_v"] == pytest.approx(us_ref, rel=0.05)
+
+
+def test_read_moments_match_oracle_macro(lbm):
+    nx, ny = 40, 36
+    rv, rl = lbm.maxwell(0.75)
+    rho0 = synth.density_field(nx, ny, "bubble", rl, rv, 9, seed=9)
+    p = lbm.make_params(nx, ny, 0.75, 0.7, -0.5, 0.5, "bgk", "edm", "fp64")
+    with lbm.Lattice(p) as lat:
+        lat.init_density(rho0)
+        lat.step(77)
+        rho, vx, vy = lat.read_moments()
+    q = oracle.params(nx, ny, 0.75, 0.7, -0.5, 0.5, "bgk", "edm")
+    f_ref, _ = oracle.run(q, oracle.init_rest(rho0), 77)
+    m, _ = oracle.macro(q, f_ref)
+    np.testing.assert_allclose(rho, m["rho"], rtol=1e-12)
+    np.testing.assert_allclose(vx, m["vx"], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(vy, m["vy"], rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_full_size_4096_sampled_nodes(lbm, precision):
+    """The bench workload at full size (4096^2, 16x16 droplets of R = 80,
+    T/Tc = 0.7, tau = 0.8, MRT + Guo, default launch configuration) for 4
+    steps; rho and v at 64 sampled nodes against the oracle run on the
+    periodic 19x19 window around each node.  One step couples a node to its
+    2-ring (streaming + the psi stencil) and v adds one more ring, so after
+    4 steps the centre of the window depends only on nodes within 9 of it."""
+    n, steps, tr, tau, A = 4096, 4, 0.7, 0.8, -0.304
+    rv, rl = lbm.maxwell(tr)
+    rho0 = synth.density_field(n, n, "droplet_array", rl, rv, 80.0, seed=20143000, cell=256)
+    p = lbm.make_params(n, n, tr, tau, A, 1.0, "mrt", "guo", precision, **MRT)
+    with lbm.Lattice(p) as lat:
+        lat.init_density(rho0)
+        lat.step(steps)
+        rho, vx, vy = lat.read_moments()
+        assert lat.variant == 1
+    rng = np.random.default_rng(4096)
+    pts = [(int(y), int(x)) for y, x in rng.integers(0, n, size=(60, 2))]
+    pts += [(0, 0), (n - 1, n - 1), (128, 128 - 80), (2048, 2048 + 80)]   # corners and interfaces
+    h = 2 * steps + 1
+    q = oracle.params(2 * h + 1, 2 * h + 1, tr, tau, A, 1.0, "mrt", "guo", **MRT)
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    for y, x in pts:
+        ys = (np.arange(y - h, y + h + 1)) % n
+        xs = (np.arange(x - h, x + h + 1)) % n
+        win = rho0[np.ix_(ys, xs)]
+        f, _ = oracle.run(q, oracle.init_rest(win), steps)
+        m, _ = oracle.macro(q, f)
+        assert abs(rho[y, x] - m["rho"][h, h]) / m["rho"][h, h] < tol
+        assert abs(vx[y, x] - m["vx"][h, h]) < 1e-13 + 1e-6 * (precision == "fp32")
+        assert abs(vy[y, x] - m["vy"][h, h]) < 1e-13 + 1e-6 * (precision == "fp32")

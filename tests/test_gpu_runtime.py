@@ -1,0 +1,216 @@
+"""Runtime behaviour of the CUDA path through the C ABI: conservation and
+determinism of the FP64 reductions, population I/O, checkpoints, presets,
+run-to-steady, and failure detection (host-side fault injection only)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1412_5170_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+MRT = dict(s_e=0.8, s_eps=0.8, s_q=1.1)
+
+
+def lattice(lbm, nx=64, ny=48, precision="fp64", coll="mrt", tr=0.8, tau=0.9, A=-0.304, K=1.0, **kw):
+    p = lbm.make_params(nx, ny, tr, tau, A, K, coll, "guo", precision, **MRT, **kw)
+    return lbm.Lattice(p)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
+def test_mass_is_conserved(lbm, precision, tol):
+    with lattice(lbm, precision=precision) as lat:
+        lat.init_preset("droplet", 12.0, seed=1)
+        m0 = lat.stats()["mass"]
+        lat.step(1000)
+        st = lat.stats()
+    assert st["status"] == 0
+    assert abs(st["mass"] - m0) / m0 < tol
+
+
+def test_runs_are_bitwise_deterministic(lbm):
+    out = []
+    for _ in range(2):
+        with lattice(lbm, 96, 64, "fp32") as lat:
+            lat.init_preset("droplet", 20.0, seed=5)
+            lat.stats(snapshot=True)
+            lat.step(300)
+            out.append((lat.read_populations(), lat.stats()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
+
+
+def test_stats_match_host_reductions(lbm):
+    with lattice(lbm, 80, 60) as lat:
+        lat.init_preset("slab", 15.0, seed=2)
+        lat.step(50)
+        st = lat.stats()
+        rho, vx, vy = lat.read_moments()
+    assert st["mass"] == pytest.approx(rho.sum(), rel=1e-14)
+    assert st["max_v"] == pytest.approx(np.hypot(vx, vy).max(), rel=1e-14)
+    assert st["rho_min"] == rho.min() and st["rho_max"] == rho.max()
+    assert st["rho_center"] == rho[30, 40] and st["rho_corner"] == rho[0, 0]
+    assert st["rho_row_mid"] == pytest.approx(rho[30].mean(), rel=1e-14)
+    assert st["rho_row0"] == pytest.approx(rho[0].mean(), rel=1e-14)
+    assert st["steps"] == 50 and st["max_dv"] == -1.0
+
+
+def test_snapshot_difference(lbm):
+    with lattice(lbm, 64, 64) as lat:
+        lat.init_preset("droplet", 16.0, seed=3)
+        lat.step(10)
+        _, vx0, vy0 = lat.read_moments()
+        lat.stats(snapshot=True)
+        lat.step(25)
+        _, vx1, vy1 = lat.read_moments()
+        st = lat.stats()
+    assert st["max_dv"] == pytest.approx(np.hypot(vx1 - vx0, vy1 - vy0).max(), rel=1e-13)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_population_roundtrip(lbm, precision):
+    f = synth.random_populations(36, 20, seed=8)
+    with lattice(lbm, 36, 20, precision) as lat:
+        lat.write_populations(f)
+        g = lat.read_populations()
+    if precision == "fp64":
+        assert np.array_equal(f, g)
+    else:
+        assert np.abs(f - g).max() < 1e-7 * np.abs(f).max()
+
+
+def test_write_populations_then_step_matches_oracle(lbm):
+    f = synth.random_populations(24, 20, seed=12, base=0.25, amp=0.1)
+    with lattice(lbm, 24, 20, tr=0.75, A=-0.3, K=0.5) as lat:
+        lat.write_populations(f)
+        lat.step(5)
+        g = lat.read_populations()
+    q = oracle.params(24, 20, 0.75, 0.9, -0.3, 0.5, "mrt", "guo", **MRT)
+    ref, _ = oracle.run(q, f, 5)
+    assert np.abs(g - ref).max() / np.abs(ref).max() < 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_checkpoint_resume_is_bitwise(lbm, tmp_path, precision):
+    path = tmp_path / "ck.lbm"
+    with lattice(lbm, 68, 44, precision) as a:
+        a.init_preset("droplet", 11.0, seed=4)
+        a.step(40)
+        a.save(path)
+        a.step(40)
+        fa = a.read_populations()
+    with lattice(lbm, 68, 44, precision) as b:
+        b.load(path)
+        assert b.stats()["steps"] == 40
+        b.step(40)
+        fb = b.read_populations()
+    assert np.array_equal(fa, fb)
+
+
+def test_corrupt_or_mismatched_checkpoint_is_rejected(lbm, tmp_path):
+    path = tmp_path / "ck.lbm"
+    with lattice(lbm, 32, 32) as a:
+        a.init_preset("droplet", 8.0)
+        a.save(path)
+    raw = bytearray(path.read_bytes())
+    raw[-5] ^= 0xFF
+    bad = tmp_path / "bad.lbm"
+    bad.write_bytes(bytes(raw))
+    with lattice(lbm, 32, 32) as b:
+        with pytest.raises(lbm.LbmError) as e:
+            b.load(bad)
+        assert e.value.status == lbm.E_IO
+    with lattice(lbm, 32, 36) as c:
+        with pytest.raises(lbm.LbmError):
+            c.load(path)
+    (tmp_path / "short.lbm").write_bytes(bytes(raw[:100]))
+    with lattice(lbm, 32, 32) as d:
+        with pytest.raises(lbm.LbmError):
+            d.load(tmp_path / "short.lbm")
+
+
+@pytest.mark.parametrize("kind", ["slab", "droplet", "bubble", "droplet_array"])
+def test_preset_matches_synthetic_generator(lbm, kind):
+    nx, ny = 96, 80
+    rv, rl = lbm.maxwell(0.8)
+    want = synth.density_field(nx, ny, kind, rl, rv, 13.0, width=5.0, seed=77, noise_amp=1e-5, cell=48)
+    with lattice(lbm, nx, ny) as lat:
+        lat.init_preset(kind, 13.0, width=5.0, seed=77, noise_amp=1e-5, cell=48)
+        rho, _, _ = lat.read_moments()
+    np.testing.assert_allclose(rho, want, rtol=2e-15, atol=0)
+
+
+def test_run_to_steady_converges_on_flat_interface(lbm):
+    with lattice(lbm, 8, 64, coll="bgk", tr=0.85, tau=1.0) as lat:
+        lat.init_preset("slab", 16.0)
+        st, done = lat.run_to_steady(1e-10, check_every=500, max_steps=200000)
+        s = lat.stats()
+    assert st == lbm.OK, lbm.lbm_strerror(st)
+    assert 0 < done < 200000 and s["max_dv"] < 1e-10
+
+
+def test_run_to_steady_reports_not_converged(lbm):
+    with lattice(lbm, 32, 32) as lat:
+        lat.init_preset("droplet", 8.0)
+        st, done = lat.run_to_steady(1e-30, check_every=10, max_steps=50)
+    assert st == lbm.E_NOT_CONVERGED and done == 50
+
+
+def test_nonfinite_input_is_detected(lbm):
+    """Fault injection on the host: a NaN in the initial density."""
+    rho0 = np.full((16, 16), 0.2)
+    rho0[3, 5] = np.nan
+    with lattice(lbm, 16, 16, "fp32") as lat:
+        lat.init_density(rho0)
+        lat.step(3)
+        st = lat.stats()
+        assert st["status"] in (lbm.E_NONFINITE, lbm.E_EOS_DOMAIN)
+        code, _ = lat.run_to_steady(1e-9, 10, 100)
+        assert code in (lbm.E_NONFINITE, lbm.E_EOS_DOMAIN)
+
+
+def test_eos_domain_violation_is_detected(lbm):
+    """rho >= 1 is outside the Carnahan-Starling domain (eta = rho < 1)."""
+    rho0 = np.full((12, 12), 0.3)
+    rho0[6, 6] = 1.2
+    with lattice(lbm, 12, 12) as lat:
+        lat.init_density(rho0)
+        lat.step(1)
+        assert lat.stats()["status"] == lbm.E_EOS_DOMAIN
+
+
+def test_unstable_run_fails_cleanly_then_context_is_reusable(lbm):
+    """BGK at tau = 0.55, T/Tc = 0.5 with the small-eps weight blows up; the
+    library reports it, and re-initialising the same context works."""
+    with lattice(lbm, 48, 48, "fp64", coll="bgk", tr=0.5, tau=0.55, A=-0.152) as lat:
+        lat.init_preset("droplet", 12.0)
+        code, _ = lat.run_to_steady(1e-9, 200, 4000)
+        assert code in (lbm.E_NONFINITE, lbm.E_EOS_DOMAIN)
+        rv, rl = lbm.maxwell(0.5)
+        lat.init_density(np.full((48, 48), rv))
+        lat.step(10)
+        assert lat.stats()["status"] == 0
+
+
+def test_workspace_from_library_allocation(lbm):
+    p = lbm.make_params(32, 32, 0.8, 0.9, -0.304, collision="mrt", **MRT)
+    a = lbm.Lattice(p, torch_workspace=False)
+    b = lbm.Lattice(p, torch_workspace=True)
+    for lat in (a, b):
+        lat.init_preset("droplet", 8.0, seed=1)
+        lat.step(20)
+    assert np.array_equal(a.read_populations(), b.read_populations())
+    a.close()
+    b.close()
+
+
+def test_variant_selection(lbm):
+    with lattice(lbm, 30, 30) as lat:
+        assert lat.variant == 0
+        with pytest.raises(lbm.LbmError):
+            lat.variant = 1
+    with lattice(lbm, 64, 30) as lat:
+        assert lat.variant == 1
+        lat.variant = 0
+        assert lat.variant == 0
