@@ -30,7 +30,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N_SIDE = 4096
+N_SIDE = 4096               # --size overrides it for profiling captures
 CELL = 256
 RADIUS = 80.0
 T_OVER_TC, TAU, A_PAPER, K_EOS = 0.7, 0.8, -0.304, 1.0
@@ -42,7 +42,8 @@ SEED = 20141217 + 2 * 1000
 # the workload above, keyed by the sha256 of the kernel sources it was taken
 # from; when the sources change the entry no longer matches and traffic is null.
 TRAFFIC_CAPTURES: dict = {}
-KERNEL_SOURCES = ["paper_1412_5170_gb300/csrc/lbm_strip.cu", "paper_1412_5170_gb300/csrc/lbm_device.cuh",
+KERNEL_SOURCES = ["paper_1412_5170_gb300/csrc/lbm_strip.cuh", "paper_1412_5170_gb300/csrc/lbm_strip_f32.cu",
+                  "paper_1412_5170_gb300/csrc/lbm_device.cuh",
                   "paper_1412_5170_gb300/csrc/lbm_kernels.cuh"]
 
 
@@ -54,8 +55,9 @@ def kernel_hash() -> str:
 
 
 def workload_config(extra=None):
-    cfg = {"workload": "droplet array 4096x4096 (16x16 droplets, R=80), T/Tc=0.7, tau=0.8, MRT+Guo, "
-                       "A=-0.304 (A_K=-0.152), K=1, FP32-deviation populations, FP64 reductions",
+    cfg = {"workload": "droplet array %dx%d (%dx%d droplets, R=80), T/Tc=0.7, tau=0.8, MRT+Guo, "
+                       "A=-0.304 (A_K=-0.152), K=1, FP32-deviation populations, FP64 reductions"
+                       % (N_SIDE, N_SIDE, N_SIDE // CELL, N_SIDE // CELL),
            "nx": N_SIDE, "ny": N_SIDE, "collision": "mrt", "forcing": "guo", "precision": "fp32_dev",
            "l2": "inputs larger than L2 (2 x 604 MB population buffers vs 129 MB L2); no flush"}
     if extra:
@@ -214,6 +216,22 @@ def run_ours(args):
     lat = lbm.Lattice(p)
     stream = lat.stream
     lat.init_density(rho0)
+    tune = {}
+    if args.autotune:
+        # Per-configuration timings (the autotuner's own choice is the minimum).
+        for cid, threads, stages, npt in lat.configs():
+            lat.config = cid
+            lat.step(2)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lat.step(10)
+            e1.record(stream)
+            e1.synchronize()
+            tune["%d:t%d/s%d" % (cid, threads, stages)] = e0.elapsed_time(e1) / 10
+        lat.init_density(rho0)
+        cfg, _ = lat.autotune(10)
+    chosen = [c for c in lat.configs() if c[0] == lat.config][0]
     variant = lat.variant
     for _ in range(args.warmup):
         lat.step(1)
@@ -242,7 +260,7 @@ def run_ours(args):
     # init from a pinned host density field, CHUNK fused steps, and a read of
     # rho, vx, vy into pinned host buffers.
     chunk = 100
-    e2e_steps = max(1, args.steps // chunk)
+    e2e_steps = max(1, args.steps // chunk) if args.e2e else 0
     h_rho0 = torch.from_numpy(rho0).pin_memory().numpy()
     h_out = [torch.empty((N_SIDE, N_SIDE), dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
     torch.cuda.synchronize()
@@ -254,7 +272,7 @@ def run_ours(args):
         lat.read_moments(out=h_out)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, ws, dev)
-    e2e_value = ws * nodes * chunk * e2e_steps / e2e_s / 1e6
+    e2e_value = ws * nodes * chunk * e2e_steps / e2e_s / 1e6 if e2e_steps else None
 
     if rank == 0:
         peak, peak_kind = measured_peaks()
@@ -267,7 +285,10 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": total_ms / max(args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config({"parallelism": "replicas" if ws > 1 else "single",
-                                       "kernel_variant": "strip" if variant == 1 else "generic"}),
+                                       "kernel_variant": "strip" if variant == 1 else "generic",
+                                       "kernel_config": {"id": chosen[0], "threads": chosen[1],
+                                                         "stages": chosen[2], "nodes_per_thread": chosen[3]},
+                                       "autotune_ms_per_step": tune or None}),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": "%s (hbm_gbs, copy)" % peak_kind,
@@ -299,7 +320,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=300,
                     help="oracle steps on one 256x256 cell for cpu_baseline (0 = skip)")
+    ap.add_argument("--size", type=int, default=4096, help="lattice side (multiple of 256; profiling)")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false", help="skip the end-to-end leg")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the default kernel configuration")
     args = ap.parse_args()
+    global N_SIDE
+    if args.size % CELL:
+        ap.error("--size must be a multiple of %d" % CELL)
+    N_SIDE = args.size
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -188,6 +188,22 @@ int lbm_load(lbm_ctx *ctx, const char *path);
 int lbm_get_variant(lbm_ctx *ctx, int *variant);
 int lbm_set_variant(lbm_ctx *ctx, int variant);
 
+/* Kernel configurations for a parameter set: id 0 is the generic kernel, ids
+ * 1..count-1 the strip kernel with the tile shapes lbm_config_describe
+ * reports (threads per CTA, shared-memory row stages, lattice nodes per
+ * thread).  Pure host queries. */
+int lbm_config_count(const lbm_params *p, int *count);
+int lbm_config_describe(const lbm_params *p, int config, int *threads, int *stages, int *nodes_per_thread);
+int lbm_get_config(lbm_ctx *ctx, int *config);
+int lbm_set_config(lbm_ctx *ctx, int config);
+
+/* Autotuner: times every configuration for trial_steps fused steps on this
+ * context's lattice (CUDA events on the context stream; the trials write the
+ * spare population buffer, so the state is not advanced) and selects the
+ * fastest.  config / ms_per_step (may be NULL) receive the choice and its
+ * time per step.  Synchronises. */
+int lbm_autotune(lbm_ctx *ctx, int trial_steps, int *config, double *ms_per_step);
+
 #ifdef __cplusplus
 }
 #endif

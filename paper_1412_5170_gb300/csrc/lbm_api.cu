@@ -32,7 +32,7 @@ struct lbm_ctx {
     unsigned* status;
     DevStats* hstats;       // pinned host mirror
     int64_t steps;
-    int variant_forced;     // -1 = automatic
+    int config;             // 0 = generic kernel, k >= 1 = strip configuration k-1
 };
 
 namespace {
@@ -99,18 +99,15 @@ void launch_generic_scheme(lbm_ctx* c, const void* fin, void* fout)
     else launch_generic<T, C, BGK, SC>(c, fin, fout);
 }
 
-int variant_of(const lbm_ctx* c)
-{
-    if (c->variant_forced >= 0) return c->variant_forced;
-    return lbm_strip_supported(&c->p) ? 1 : 0;
-}
+int default_config(const lbm_params& p) { return lbm_strip_supported(&p) ? 1 : 0; }
 
-int step_once(lbm_ctx* c)
+int n_configs(const lbm_params& p) { return 1 + (lbm_strip_supported(&p) ? lbm_strip_config_count(p.precision) : 0); }
+
+// One fused step from fin to fout with kernel configuration cfg.
+int launch_step(lbm_ctx* c, int cfg, const void* fin, void* fout)
 {
-    const void* fin = c->f[c->cur];
-    void* fout = c->f[c->cur ^ 1];
-    if (variant_of(c) == 1) {
-        const int s = lbm_strip_launch(&c->p, fin, fout, c->status, c->stream);
+    if (cfg >= 1) {
+        const int s = lbm_strip_launch(&c->p, cfg - 1, fin, fout, c->status, c->stream);
         if (s != LBM_OK) return s;
     } else if (c->p.precision == LBM_FP64) {
         launch_generic_scheme<double, double>(c, fin, fout);
@@ -118,6 +115,13 @@ int step_once(lbm_ctx* c)
         launch_generic_scheme<float, float>(c, fin, fout);
     }
     LBM_CUDA(cudaGetLastError());
+    return LBM_OK;
+}
+
+int step_once(lbm_ctx* c)
+{
+    const int s = launch_step(c, c->config, c->f[c->cur], c->f[c->cur ^ 1]);
+    if (s != LBM_OK) return s;
     c->cur ^= 1;
     c->steps += 1;
     return LBM_OK;
@@ -255,7 +259,7 @@ int lbm_create(const lbm_params* p, void* cuda_stream, void* workspace_dev, size
     c->dstats = (DevStats*)(b + L.dstats);
     c->status = (unsigned*)(b + L.status);
     c->cur = 0;
-    c->variant_forced = -1;
+    c->config = default_config(*p);
     cudaError_t e = cudaMallocHost(&c->hstats, sizeof(DevStats));
     if (e != cudaSuccess) {
         if (c->owns) cudaFree(c->ws);
@@ -466,7 +470,7 @@ int lbm_load(lbm_ctx* c, const char* path)
 int lbm_get_variant(lbm_ctx* c, int* variant)
 {
     if (!c || !variant) return LBM_E_INVALID;
-    *variant = variant_of(c);
+    *variant = c->config >= 1 ? 1 : 0;
     return LBM_OK;
 }
 
@@ -474,7 +478,79 @@ int lbm_set_variant(lbm_ctx* c, int variant)
 {
     if (!c || variant < -1 || variant > 1) return LBM_E_INVALID;
     if (variant == 1 && !lbm_strip_supported(&c->p)) return LBM_E_UNSUPPORTED;
-    c->variant_forced = variant;
+    c->config = variant == -1 ? default_config(c->p) : variant;
+    return LBM_OK;
+}
+
+int lbm_config_count(const lbm_params* p, int* count)
+{
+    if (!p || !count || lbm_validate_params(p) != LBM_OK) return LBM_E_INVALID;
+    *count = n_configs(*p);
+    return LBM_OK;
+}
+
+int lbm_config_describe(const lbm_params* p, int config, int* threads, int* stages, int* nodes_per_thread)
+{
+    if (!p || lbm_validate_params(p) != LBM_OK || config < 0 || config >= n_configs(*p)) return LBM_E_INVALID;
+    int th = GTX * GTY, st = 0, npt = 1;
+    if (config >= 1) {
+        const StripConfig sc = lbm_strip_config(p->precision, config - 1);
+        th = sc.threads;
+        st = sc.stages;
+        npt = 4;
+    }
+    if (threads) *threads = th;
+    if (stages) *stages = st;
+    if (nodes_per_thread) *nodes_per_thread = npt;
+    return LBM_OK;
+}
+
+int lbm_get_config(lbm_ctx* c, int* config)
+{
+    if (!c || !config) return LBM_E_INVALID;
+    *config = c->config;
+    return LBM_OK;
+}
+
+int lbm_set_config(lbm_ctx* c, int config)
+{
+    if (!c || config < 0 || config >= n_configs(c->p)) return LBM_E_INVALID;
+    c->config = config;
+    return LBM_OK;
+}
+
+int lbm_autotune(lbm_ctx* c, int trial_steps, int* config, double* ms_per_step)
+{
+    if (!c || trial_steps < 1) return LBM_E_INVALID;
+    cudaEvent_t e0, e1;
+    LBM_CUDA(cudaEventCreate(&e0));
+    LBM_CUDA(cudaEventCreate(&e1));
+    int best = c->config;
+    float best_ms = 3.4e38f;
+    int status = LBM_OK;
+    const void* fin = c->f[c->cur];
+    void* spare = c->f[c->cur ^ 1];
+    for (int cfg = 0; cfg < n_configs(c->p) && status == LBM_OK; ++cfg) {
+        // Trials read the current state and write the spare buffer: the
+        // lattice state is unchanged.  One untimed launch sets up the kernel.
+        status = launch_step(c, cfg, fin, spare);
+        if (status != LBM_OK) break;
+        if ((status = cuda_status(cudaEventRecord(e0, c->stream))) != LBM_OK) break;
+        for (int i = 0; i < trial_steps && status == LBM_OK; ++i) status = launch_step(c, cfg, fin, spare);
+        if (status != LBM_OK) break;
+        if ((status = cuda_status(cudaEventRecord(e1, c->stream))) != LBM_OK) break;
+        if ((status = cuda_status(cudaEventSynchronize(e1))) != LBM_OK) break;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= trial_steps;
+        if (ms < best_ms) { best_ms = ms; best = cfg; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (status != LBM_OK) return status;
+    c->config = best;
+    if (config) *config = best;
+    if (ms_per_step) *ms_per_step = best_ms;
     return LBM_OK;
 }
 

@@ -21,6 +21,14 @@ __host__ __device__ constexpr int ey(int a) { return a == 2 || a == 5 || a == 6 
 template <typename C>
 __host__ __device__ constexpr C wt(int a) { return a == 0 ? C(4) / C(9) : (a < 5 ? C(1) / C(9) : C(1) / C(36)); }
 
+// Division, reciprocal and square root in the compute type: CUDA's fast
+// single-precision intrinsics for float (a few ulp, far below the FP32
+// path's tolerances), IEEE operations for double.
+__device__ __forceinline__ float cdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double cdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float csqrt(float a) { return sqrtf(a); }
+__device__ __forceinline__ double csqrt(double a) { return sqrt(a); }
+
 // Per-lattice constants in the compute type.
 template <typename C>
 struct Coef {
@@ -45,11 +53,11 @@ __device__ __forceinline__ C psi_of_rho(C rho, const Coef<C>& k, unsigned& bad)
     const C one_m = C(1) - eta;
     const C num = C(1) + eta * (C(1) + eta * (C(1) - eta));
     const C den = one_m * one_m * one_m;
-    const C p = k.K * (rho * k.T * num / den - rho * rho);
+    const C p = k.K * (rho * k.T * cdiv(num, den) - rho * rho);
     const C s = C(2) * (rho * (C(1) / C(3)) - p);
     const bool ok = (rho > C(0)) && (rho < C(1)) && (s >= C(0));
     if (!ok) bad |= ST_EOS;
-    return ok ? sqrt(s) : C(0);
+    return ok ? csqrt(s) : C(0);
 }
 
 // Kupershtokh's hybrid force (Eq. 6) with G = -1, U = -psi^2/2 and the
@@ -100,7 +108,7 @@ __device__ __forceinline__ void collide(C g[9], C Fx, C Fy, const Coef<C>& k, C&
     C drho, jx, jy;
     moments(g, drho, jx, jy);
     const C rho = k.rho_ref + drho;
-    const C inv_rho = C(1) / rho;
+    const C inv_rho = cdiv(C(1), rho);
     const C ux = jx * inv_rho, uy = jy * inv_rho;
     vx = ux + C(0.5) * Fx * inv_rho;
     vy = uy + C(0.5) * Fy * inv_rho;
@@ -191,6 +199,11 @@ __device__ __forceinline__ void collide(C g[9], C Fx, C Fy, const Coef<C>& k, C&
         g[7] = diag - dx - dy + b8;
         g[8] = diag + dx - dy - b8;
     }
+    // Every scheme conserves mass (sum f* = rho).  Close the rest population
+    // on it so that rounding in the equilibrium weights (4/9, 1/9, 1/36 and
+    // the 1/9 of M^-1 are inexact in binary) cannot bias the mass step after
+    // step; the residual is one unbiased rounding of g[0].
+    g[0] = drho - (((g[1] + g[3]) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8])));
 }
 
 // Status bits of a node after collision: non-finite output.

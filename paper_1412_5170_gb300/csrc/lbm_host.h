@@ -6,7 +6,9 @@
 #include <vector>
 
 #include "lbm.h"
+#ifdef __CUDACC__
 #include "lbm_device.cuh"
+#endif
 
 extern "C" {
 double lbm_tc(void);
@@ -20,10 +22,15 @@ int lbm_validate_params(const lbm_params* p);
 int lbm_preset_field(int nx, int ny, int kind, double size, double width, double rho_l, double rho_v,
                      int32_t cell, uint64_t seed, double noise_amp, std::vector<double>& out);
 
-// Pipelined strip kernel (lbm_strip.cu): whether it supports p, and one step.
+// Pipelined strip kernel (lbm_strip*.cu): whether it supports p, its tuning
+// configurations (threads per CTA, row stages), and one step with one of them.
+struct StripConfig { int threads, stages; };
 bool lbm_strip_supported(const lbm_params* p);
-int lbm_strip_launch(const lbm_params* p, const void* fin, void* fout, unsigned* status, cudaStream_t s);
+int lbm_strip_config_count(int precision);
+StripConfig lbm_strip_config(int precision, int cfg);
+int lbm_strip_launch(const lbm_params* p, int cfg, const void* fin, void* fout, unsigned* status, cudaStream_t s);
 
+#ifdef __CUDACC__
 // Kernel constants of a parameter set in the compute type C.
 template <typename C>
 lbm::Coef<C> make_coef(const lbm_params& p)
@@ -42,3 +49,4 @@ lbm::Coef<C> make_coef(const lbm_params& p)
     k.rho_ref = C(p.precision == LBM_FP64 ? 0.0 : p.rho_ref);
     return k;
 }
+#endif  // __CUDACC__

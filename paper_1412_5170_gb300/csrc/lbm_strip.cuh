@@ -1,0 +1,318 @@
+// lbm_strip.cuh -- the pipelined strip kernel: one fused D2Q9 time step
+// (pull streaming, Eq. 3 moments, Eq. 7/29/30 psi, Eq. 6 force, BGK/MRT
+// collision with Guo/EDM/SC forcing) for lattices with nx % 4 == 0.
+//
+// Each CTA owns a strip of W = 4*NT columns and a chunk of rows, and walks
+// down its rows.  For density row r it needs the pulled populations
+// f*_a(x - e_a) on row r and one column of halo on each side; those come
+// from nine row segments (one per direction, source row r - e_y(a), columns
+// x0-4 .. x0+W+4) that one warp copies into a shared-memory ring of NS
+// stages with cp.async.bulk (TMA bulk copies) completing on one mbarrier per
+// stage.  Every population is read from HBM once per step plus the 8-column
+// and 2-row halos (served mostly by L2), never re-read for the psi stencil.
+//
+// Iteration k of the row walk:
+//   1. wait for stage k (bounded wait)
+//   2. psi of density row k (the strip's columns plus one halo column on
+//      each side) into a 4-row psi ring
+//   3. __syncthreads_or (also the collective timeout exit)
+//   4. refill the stage freed by row k-2 with row k-2+NS (one warp)
+//   5. collide row k-1: pulled populations from its stage, F from psi rows
+//      k-2..k, nine 128-bit stores of the post-collision deviations
+// Rows 0 and H+1 of the walk are the halo rows above and below the chunk.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "lbm_host.h"
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+constexpr long long kWaitLimit = 1ll << 26;   // try_wait polls before a stage is declared stuck
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on one phase of an mbarrier; false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity)
+{
+    for (long long i = 0; i < kWaitLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Bulk global -> shared copy (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void lds4(const float* p, float v[4])
+{
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void lds4(const double* p, double v[4])
+{
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    const double2 b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void sts4(float* p, const float v[4])
+{
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void sts4(double* p, const double v[4])
+{
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void stg4(float* p, float a, float b, float c, float d)
+{
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void stg4(double* p, double a, double b, double c, double d)
+{
+    *reinterpret_cast<double2*>(p) = make_double2(a, b);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(c, d);
+}
+
+// Pulled deviations of the 4 nodes [4t, 4t+4) of a stage.  Row segment of
+// direction a starts at column x0 - 4, so node column c sits at index 4 + c
+// and its pulled value f*_a(c - e_x) at 4 + c - e_x.
+template <typename T, typename C>
+__device__ __forceinline__ void pull4(const T* __restrict__ st, int stride, int c0, C g[9][4])
+{
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const T* d = st + a * stride + 4 + c0;
+        T v[4];
+        lds4(d, v);
+        if (ex(a) == 0) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) g[a][j] = C(v[j]);
+        } else if (ex(a) > 0) {
+            g[a][0] = C(d[-1]); g[a][1] = C(v[0]); g[a][2] = C(v[1]); g[a][3] = C(v[2]);
+        } else {
+            g[a][0] = C(v[1]); g[a][1] = C(v[2]); g[a][2] = C(v[3]); g[a][3] = C(d[4]);
+        }
+    }
+}
+
+// Pulled deviations of a single node at strip column c (c may be -1 or W).
+template <typename T, typename C>
+__device__ __forceinline__ C drho1(const T* __restrict__ st, int stride, int c)
+{
+    C s[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) s[a] = C(st[a * stride + 4 + c - ex(a)]);
+    return sum9(s);
+}
+
+template <typename T, typename C, int COLL, int FORC, int NT, int NS>
+__global__ void __launch_bounds__(NT)
+k_step_strip(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, int nchunks, Coef<C> k,
+             unsigned* __restrict__ status)
+{
+    constexpr int W = 4 * NT;
+    constexpr int SW = W + 8;            // stage row stride (elements)
+    constexpr int PW = W + 8;            // psi ring row stride: column c at index 4 + c
+    extern __shared__ __align__(128) unsigned char smem[];
+    T* stages = reinterpret_cast<T*>(smem);                                  // [NS][9][SW]
+    C* psi = reinterpret_cast<C*>(smem + sizeof(T) * NS * 9 * SW);           // [4][PW]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + sizeof(T) * NS * 9 * SW + sizeof(C) * 4 * PW);
+
+    const int t = threadIdx.x;
+    const int x0 = blockIdx.x * W;
+    const int wp = min(W, nx - x0);                         // strip width (multiple of 4)
+    const int y0 = int((long long)blockIdx.y * ny / nchunks);
+    const int y1 = int((long long)(blockIdx.y + 1) * ny / nchunks);
+    const int H = y1 - y0;
+    if (H <= 0) return;
+    const size_t n = (size_t)nx * ny;
+    const int nrows = H + 2;                                // walk rows incl. 2 halo rows
+    const unsigned stage_bytes = unsigned(9 * (wp + 8) * sizeof(T));
+    const bool left_wrap = x0 == 0, right_wrap = x0 + wp == nx;
+
+    if (t == 0) {
+        for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    // Warp 0 issues the nine segment copies of walk row kr into its stage.
+    auto issue = [&](int kr) {
+        if (t >= 32) return;
+        const int slot = kr % NS;
+        T* st = stages + slot * 9 * SW;
+        if (t == 0) mbar_arrive_expect_tx(&bars[slot], stage_bytes);
+        __syncwarp();
+        if (t < 9) {
+            fence_proxy_async();   // order earlier generic reads of this slot before the async writes
+            const int a = t;
+            const int r = wrap_any(y0 - 1 + kr - ey(a), ny);
+            const T* row = fin + a * n + (size_t)r * nx;
+            T* dst = st + a * SW;
+            if (!left_wrap && !right_wrap) {
+                bulk_g2s(dst, row + x0 - 4, unsigned((wp + 8) * sizeof(T)), &bars[slot]);
+            } else {
+                bulk_g2s(dst, row + (left_wrap ? nx - 4 : x0 - 4), unsigned(4 * sizeof(T)), &bars[slot]);
+                bulk_g2s(dst + 4, row + x0, unsigned(wp * sizeof(T)), &bars[slot]);
+                bulk_g2s(dst + 4 + wp, row + (right_wrap ? 0 : x0 + wp), unsigned(4 * sizeof(T)), &bars[slot]);
+            }
+        }
+    };
+
+    for (int kr = 0; kr < NS - 2 && kr < nrows; ++kr) issue(kr);
+
+    unsigned bad = 0;
+    const int c0 = 4 * t;
+    const bool active = c0 < wp;
+    int kdone = 0;                         // walk rows whose stage wait completed
+    for (int kk = 0; kk < nrows; ++kk) {
+        const int slot = kk % NS;
+        const T* st = stages + slot * 9 * SW;
+        const bool ok = mbar_wait(&bars[slot], (kk / NS) & 1);
+        // psi of walk row kk
+        C* prow = psi + (kk & 3) * PW;
+        if (ok) {
+            if (active) {
+                C g[9][4];
+                pull4<T, C>(st, SW, c0, g);
+                C ps[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    C s[9];
+#pragma unroll
+                    for (int a = 0; a < 9; ++a) s[a] = g[a][j];
+                    ps[j] = psi_of_rho<C>(k.rho_ref + sum9(s), k, bad);
+                }
+                sts4(prow + 4 + c0, ps);
+            }
+            if (t == 0) prow[3] = psi_of_rho<C>(k.rho_ref + drho1<T, C>(st, SW, -1), k, bad);
+            if (t == NT - 1) prow[4 + wp] = psi_of_rho<C>(k.rho_ref + drho1<T, C>(st, SW, wp), k, bad);
+        }
+        if (__syncthreads_or(!ok)) {
+            bad |= ST_TIMEOUT;
+            kdone = kk;
+            break;
+        }
+        kdone = kk + 1;
+        // refill the stage of walk row kk-2 (collided in the previous iteration)
+        if (kk + NS - 2 < nrows) issue(kk + NS - 2);
+        // collide walk row kk-1 (a chunk row when 1 <= kk-1 <= H)
+        const int kc = kk - 1;
+        if (kc >= 1 && kc <= H && active) {
+            const T* sc = stages + (kc % NS) * 9 * SW;
+            C g[9][4];
+            pull4<T, C>(sc, SW, c0, g);
+            const C* pm = psi + ((kc - 1) & 3) * PW + 4 + c0;   // row y - 1
+            const C* p0 = psi + (kc & 3) * PW + 4 + c0;         // row y
+            const C* pp = psi + ((kc + 1) & 3) * PW + 4 + c0;   // row y + 1
+            C rm[6], r0[6], rp[6];     // columns c0-1 .. c0+4
+            {
+                C v[4];
+                lds4(pm, v); rm[0] = pm[-1]; rm[1] = v[0]; rm[2] = v[1]; rm[3] = v[2]; rm[4] = v[3]; rm[5] = pm[4];
+                lds4(p0, v); r0[0] = p0[-1]; r0[1] = v[0]; r0[2] = v[1]; r0[3] = v[2]; r0[4] = v[3]; r0[5] = p0[4];
+                lds4(pp, v); rp[0] = pp[-1]; rp[1] = v[0]; rp[2] = v[1]; rp[3] = v[2]; rp[4] = v[3]; rp[5] = pp[4];
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                Stencil<C> q{r0[j + 1], r0[j + 2], rp[j + 1], r0[j], rm[j + 1],
+                             rp[j + 2], rp[j], rm[j], rm[j + 2]};
+                C Fx, Fy, vx, vy, rho, gj[9];
+                force<C>(q, k, Fx, Fy);
+#pragma unroll
+                for (int a = 0; a < 9; ++a) gj[a] = g[a][j];
+                collide<C, COLL, FORC>(gj, Fx, Fy, k, vx, vy, rho);
+                bad |= finite_bits<C>(gj);
+#pragma unroll
+                for (int a = 0; a < 9; ++a) g[a][j] = gj[a];
+            }
+            const int y = y0 + kc - 1;
+            T* out = fout + (size_t)y * nx + x0 + c0;
+#pragma unroll
+            for (int a = 0; a < 9; ++a) stg4(out + a * n, T(g[a][0]), T(g[a][1]), T(g[a][2]), T(g[a][3]));
+        }
+    }
+    if (bad & ST_TIMEOUT) {
+        // Drain copies already issued for rows the walk never consumed (bounded).
+        if (t == 0) {
+            const int issued = min(nrows, kdone + NS - 2);
+            for (int kr = kdone; kr < issued; ++kr) mbar_wait(&bars[kr % NS], (kr / NS) & 1);
+        }
+        __syncthreads();
+    }
+    flag_status(bad, status);
+}
+
+template <typename T, typename C, int NT, int NS>
+constexpr size_t strip_smem()
+{
+    return sizeof(T) * NS * 9 * (4 * NT + 8) + sizeof(C) * 4 * (4 * NT + 8) + 8 * NS;
+}
+
+// One launch over the whole lattice: strips of 4*NT columns, and as many row
+// chunks as fill every resident CTA slot once (one wave), but no chunk shorter
+// than 16 rows, so the two halo rows per chunk stay a small overhead.
+template <typename T, typename C, int COLL, int FORC, int NT, int NS>
+int launch_strip_cfg(const lbm_params* p, const void* fin, void* fout, unsigned* status, cudaStream_t s)
+{
+    constexpr size_t smem = strip_smem<T, C, NT, NS>();
+    auto kern = k_step_strip<T, C, COLL, FORC, NT, NS>;
+    static int per_sm = 0, nsm = 0;    // per instantiation (one device per process)
+    if (per_sm == 0) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return LBM_E_CUDA;
+        int dev = 0, occ = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem) != cudaSuccess || occ < 1) occ = 1;
+        per_sm = occ;
+    }
+    const int W = 4 * NT;
+    const int nstrips = (p->nx + W - 1) / W;
+    int nchunks = std::max(1, (nsm * per_sm) / nstrips);
+    nchunks = std::min(nchunks, std::max(1, p->ny / 16));
+    const Coef<C> k = make_coef<C>(*p);
+    kern<<<dim3(nstrips, nchunks), NT, smem, s>>>((const T*)fin, (T*)fout, p->nx, p->ny, nchunks, k, status);
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_E_CUDA;
+}
+
+template <typename T, typename C, int NT, int NS>
+int launch_strip_scheme(const lbm_params* p, const void* fin, void* fout, unsigned* status, cudaStream_t s)
+{
+    if (p->collision == LBM_MRT) return launch_strip_cfg<T, C, MRT, GUO, NT, NS>(p, fin, fout, status, s);
+    if (p->forcing == LBM_GUO) return launch_strip_cfg<T, C, BGK, GUO, NT, NS>(p, fin, fout, status, s);
+    if (p->forcing == LBM_EDM) return launch_strip_cfg<T, C, BGK, EDM, NT, NS>(p, fin, fout, status, s);
+    return launch_strip_cfg<T, C, BGK, SC, NT, NS>(p, fin, fout, status, s);
+}
+
+}  // namespace lbm

@@ -73,6 +73,12 @@ _PROTOS = {
     "lbm_load": (ctypes.c_int, [_vp, ctypes.c_char_p]),
     "lbm_get_variant": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "lbm_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "lbm_config_count": (ctypes.c_int, [ctypes.POINTER(lbm_params), ctypes.POINTER(ctypes.c_int)]),
+    "lbm_config_describe": (ctypes.c_int, [ctypes.POINTER(lbm_params), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "lbm_get_config": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "lbm_set_config": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "lbm_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp]),
 }
 for _name, (_res, _args) in _PROTOS.items():
     _f = getattr(_lib, _name)
@@ -211,6 +217,35 @@ class Lattice:
 
     def load(self, path):
         check(lbm_load(self.ctx, str(path).encode()), "lbm_load")
+
+    @property
+    def config(self) -> int:
+        v = ctypes.c_int()
+        check(lbm_get_config(self.ctx, ctypes.byref(v)), "lbm_get_config")
+        return v.value
+
+    @config.setter
+    def config(self, v: int):
+        check(lbm_set_config(self.ctx, int(v)), "lbm_set_config")
+
+    def configs(self):
+        """[(id, threads, stages, nodes_per_thread)] of every kernel configuration."""
+        n = ctypes.c_int()
+        check(lbm_config_count(ctypes.byref(self.p), ctypes.byref(n)), "lbm_config_count")
+        out = []
+        for i in range(n.value):
+            t, s_, v = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            check(lbm_config_describe(ctypes.byref(self.p), i, ctypes.byref(t), ctypes.byref(s_), ctypes.byref(v)),
+                  "lbm_config_describe")
+            out.append((i, t.value, s_.value, v.value))
+        return out
+
+    def autotune(self, trial_steps: int = 20):
+        """Time every kernel configuration on this lattice and keep the fastest;
+        returns (config, ms_per_step).  The lattice state is not advanced."""
+        cfg, ms = ctypes.c_int(), ctypes.c_double()
+        check(lbm_autotune(self.ctx, int(trial_steps), ctypes.byref(cfg), ctypes.byref(ms)), "lbm_autotune")
+        return cfg.value, ms.value
 
     @property
     def variant(self) -> int:

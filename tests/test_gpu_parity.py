@@ -85,7 +85,7 @@ def test_fp32_deviation_matches_oracle_elementwise(lbm, coll, forc, variant):
     f_gpu, f_ref, st, ost = run_pair(lbm, nx, ny, steps, coll, forc, precision="fp32", variant=variant)
     assert st["status"] == 0
     rho_g, rho_r = f_gpu.sum(0), f_ref.sum(0)
-    assert np.abs(rho_g - rho_r).max() / rho_r.min() < 2e-5
+    assert (np.abs(rho_g - rho_r) / rho_r).max() < 2e-5
 
 
 def test_strip_and_generic_agree(lbm):
@@ -97,10 +97,12 @@ def test_strip_and_generic_agree(lbm):
         assert np.abs(out[0] - out[1]).max() / np.abs(out[0]).max() < tol
 
 
-def test_fp32_coexistence_and_spurious_velocity(lbm):
+def test_fp32_flat_interface_coexistence(lbm):
     """North-star FP32 bar on the 64x64 slab (BGK + Guo, T/Tc = 0.8): after
     10000 steps the FP32-deviation coexistence densities agree with the FP64
-    oracle to 1e-4 relative and Us_max to 5 %."""
+    oracle to 1e-4 relative.  (A converged flat interface has spurious
+    velocities of ~1e-9, below FP32 resolution; Us_max is compared on the
+    droplet below.)"""
     nx = ny = 64
     steps = 10000
     rv, rl = lbm.maxwell(0.8)
@@ -117,7 +119,32 @@ def test_fp32_coexistence_and_spurious_velocity(lbm):
     us_ref = np.hypot(m["vx"], m["vy"]).max()
     assert st["rho_row_mid"] == pytest.approx(rl_ref, rel=1e-4)
     assert st["rho_row0"] == pytest.approx(rv_ref, rel=1e-4)
+    assert st["max_v"] < 1e-5 and us_ref < 1e-6
+
+
+@pytest.mark.parametrize("coll", ["bgk", "mrt"])
+def test_fp32_droplet_coexistence_and_spurious_velocity(lbm, coll):
+    """North-star FP32 bar on a curved interface: droplet R = 16 on 64x64,
+    T/Tc = 0.8, tau = 1, 10000 steps.  Liquid (centre) and vapour (corner)
+    densities within 1e-4 relative of the FP64 oracle, Us_max within 5 %."""
+    nx = ny = 64
+    steps = 10000
+    rv, rl = lbm.maxwell(0.8)
+    rho0 = synth.density_field(nx, ny, "droplet", rl, rv, 16, seed=20141218)
+    p = lbm.make_params(nx, ny, 0.8, 1.0, -0.304, 1.0, coll, "guo", "fp32", **MRT)
+    with lbm.Lattice(p) as lat:
+        lat.init_density(rho0)
+        lat.step(steps)
+        st = lat.stats()
+    q = oracle.params(nx, ny, 0.8, 1.0, -0.304, 1.0, coll, "guo", **MRT)
+    f_ref, _ = oracle.run(q, oracle.init_rest(rho0), steps)
+    m, _ = oracle.macro(q, f_ref)
+    us_ref = np.hypot(m["vx"], m["vy"]).max()
+    assert st["status"] == 0
+    assert st["rho_center"] == pytest.approx(m["rho"][ny // 2, nx // 2], rel=1e-4)
+    assert st["rho_corner"] == pytest.approx(m["rho"][0, 0], rel=1e-4)
     assert st["max_v"] == pytest.approx(us_ref, rel=0.05)
+    assert us_ref > 1e-5
 
 
 def test_read_moments_match_oracle_macro(lbm):
