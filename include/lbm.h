@@ -204,6 +204,37 @@ int lbm_set_config(lbm_ctx *ctx, int config);
  * time per step.  Synchronises. */
 int lbm_autotune(lbm_ctx *ctx, int trial_steps, int *config, double *ms_per_step);
 
+/* ---- observables without allocation ----
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory: code inside a host application whose memory
+ * pool owns the device and forbids cudaMalloc/cudaFree, or loops that must
+ * not stall on an allocation (both calls may synchronise the device).
+ *
+ * lbm_stats_noalloc computes what lbm_stats(ctx, 0, out) computes, from a
+ * population buffer the caller owns, and allocates nothing: its scratch is a
+ * fixed array of LBM_NOALLOC_MAX_TILES 64-byte records (4 MiB) compiled into
+ * the library, which every GPU that loads the library keeps until the
+ * process exits.
+ *   p         parameters of the lattice (as for lbm_create)
+ *   f_dev     device buffer of 9*ny*nx values in the library's stored layout:
+ *             double (LBM_FP64) or float (LBM_FP32_DEV) post-collision
+ *             populations of the previous step in the pull convention,
+ *             f*_a(x) = f_a(x + e_a, t) - w_a rho_ref (rho_ref = 0 for FP64)
+ *   cuda_stream  stream the work is queued on; the call synchronises it
+ *   out       host struct; max_dv = -1 and steps = 0 (no context history)
+ * Limits and behaviour:
+ *   - lattices needing more than LBM_NOALLOC_MAX_TILES tiles of 32 x 8 nodes
+ *     (ceil(nx/32) * ceil(ny/8); any lattice up to 4096 x 4096 fits) are
+ *     rejected with LBM_E_UNSUPPORTED and a message on stderr;
+ *   - every call shares the one scratch array and leaves its contents
+ *     behind, so calls that overlap on the GPU (other threads or streams)
+ *     race and must be serialised by the caller;
+ *   - the first call on each device does a one-time set-up (it looks up the
+ *     scratch array's device address with that device current); make that
+ *     first call before any stream capture. */
+#define LBM_NOALLOC_MAX_TILES 65536
+int lbm_stats_noalloc(const lbm_params *p, const void *f_dev, void *cuda_stream, lbm_stats_t *out);
+
 #ifdef __cplusplus
 }
 #endif
