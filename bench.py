@@ -42,7 +42,8 @@ SEED = 20141217 + 2 * 1000
 # the workload above, keyed by the sha256 of the kernel sources it was taken
 # from; when the sources change the entry no longer matches and traffic is null.
 TRAFFIC_CAPTURES: dict = {}
-KERNEL_SOURCES = ["paper_1412_5170_gb300/csrc/lbm_strip.cuh", "paper_1412_5170_gb300/csrc/lbm_strip_f32.cu",
+KERNEL_SOURCES = ["paper_1412_5170_gb300/csrc/lbm_warp.cuh", "paper_1412_5170_gb300/csrc/lbm_strip.cuh",
+                  "paper_1412_5170_gb300/csrc/lbm_strip_f32.cu",
                   "paper_1412_5170_gb300/csrc/lbm_device.cuh",
                   "paper_1412_5170_gb300/csrc/lbm_kernels.cuh"]
 
@@ -63,6 +64,15 @@ def workload_config(extra=None):
     if extra:
         cfg.update(extra)
     return cfg
+
+
+def kernel_name(cfg):
+    cid, threads, stages, _ = cfg
+    if cid == 0:
+        return "k_step_generic<float,float,MRT,GUO>"
+    if threads == 32:
+        return "k_step_warp<float,MRT,GUO,%d>" % stages
+    return "k_step_strip<float,float,MRT,GUO,%d,%d>" % (threads, stages)
 
 
 def measured_peaks():
@@ -292,7 +302,7 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": "%s (hbm_gbs, copy)" % peak_kind,
-                         "kernel": "k_step_strip<float,float,MRT,GUO>", "kernel_ms": kernel_ms,
+                         "kernel": kernel_name(chosen), "kernel_ms": kernel_ms,
                          "bytes_per_node": BYTES_PER_NODE},
             "cpu_baseline": {"value": cpu_rate, "unit": "MLUPS", "cores": 1, "kind": "oracle",
                              "sample": "%d FP64 oracle steps on one 256x256 droplet cell (%.1f s)"

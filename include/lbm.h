@@ -204,6 +204,131 @@ int lbm_set_config(lbm_ctx *ctx, int config);
  * time per step.  Synchronises. */
 int lbm_autotune(lbm_ctx *ctx, int trial_steps, int *config, double *ms_per_step);
 
+/* ---- batched instances ----
+ * Many independent periodic lattices with their own size, T/Tc, tau, A, K and
+ * initial field (the paper's tau, T/Tc and EOS-scale sweeps, Secs. 4.2-4.4)
+ * advanced together: one kernel launch per time step covers every running
+ * instance through a table of (instance, 128-column strip, row chunk) work
+ * items, each check interval is one CUDA graph, and convergence or failure is
+ * decided per instance on the device.  Populations are FP32 deviations
+ * (precision must be LBM_FP32_DEV; rho_ref = the instance's Maxwell vapour
+ * density); every nx must be a multiple of 4.  All batch calls are
+ * synchronous; the batch owns its device memory and its CUDA stream. */
+typedef struct {
+    int32_t collision;   /* lbm_collision */
+    int32_t forcing;     /* lbm_forcing (MRT: Guo only) */
+    int32_t precision;   /* LBM_FP32_DEV */
+    int32_t reserved;    /* 0 */
+    double s_e, s_eps, s_q;   /* MRT rates shared by all instances */
+} lbm_batch_params;
+
+/* One instance: lattice, model parameters (as in lbm_params) and its initial
+ * field (as in lbm_init_preset: kind, size = radius or half-width, tanh width,
+ * rho_l / rho_v <= 0 for the Maxwell densities, droplet-array cell, noise). */
+typedef struct {
+    int32_t nx, ny, kind, cell;
+    double T_over_Tc, tau, A, K;
+    double size, width, rho_l, rho_v, noise_amp;
+    uint64_t seed;
+} lbm_instance;
+
+/* Per-instance observables returned by lbm_batch_results, in this order. */
+#define LBM_BATCH_NOBS 10  /* mass, max_v, max_dv, max_drho, rho_min, rho_max,
+                              rho_center, rho_corner, rho_row_mid, rho_row0 */
+#define LBM_RUNNING 0
+#define LBM_CONVERGED 1
+#define LBM_FAILED 2
+
+typedef struct lbm_batch lbm_batch;
+
+int lbm_batch_create(const lbm_batch_params *bp, const lbm_instance *inst, int n, lbm_batch **out);
+void lbm_batch_destroy(lbm_batch *b);
+
+/* Initial state of every instance from its preset (computed on the device),
+ * or, for instances with use_profile_host[i] != 0, from a density profile:
+ * profiles_dev is a device array [n][nb] of densities at s_k = (k + 1/2)
+ * smax/nb, s = r/R (droplet, bubble) or |y - ny/2|/h (slab), linearly
+ * interpolated and clamped at the ends (the learned warm start).  Pass
+ * profiles_dev = NULL for presets only.  Resets steps, states and snapshots. */
+int lbm_batch_init(lbm_batch *b, const double *profiles_dev, const int32_t *use_profile_host, int nb, double smax);
+
+/* nsteps time steps of every running instance (no convergence checks). */
+int lbm_batch_step(lbm_batch *b, int64_t nsteps);
+
+/* Step every running instance, checking each every check_every steps: an
+ * instance converges when max|v(t) - v(t - check_every)| < tol_v or
+ * max|rho(t) - rho(t - check_every)|/rho < tol_rho (a tolerance <= 0 is
+ * ignored) and fails when a kernel flags a non-finite or out-of-domain value;
+ * either way it stops stepping while the others go on.  Returns LBM_OK when no
+ * instance is left running, LBM_E_NOT_CONVERGED at max_steps. */
+int lbm_batch_run_to_steady(lbm_batch *b, double tol_v, double tol_rho, int64_t check_every, int64_t max_steps,
+                            int64_t *steps_done);
+
+/* Recompute the observables of every instance (no decisions, no snapshot change). */
+int lbm_batch_observe(lbm_batch *b);
+
+/* Host arrays of n entries (any may be NULL): state (LBM_RUNNING /
+ * LBM_CONVERGED / LBM_FAILED), failure code (LBM_E_*), steps taken, and
+ * n * LBM_BATCH_NOBS observables from the last check or observe. */
+int lbm_batch_results(lbm_batch *b, int32_t *state, int32_t *code, int64_t *steps, double *obs);
+
+/* FP64 density field of instance i (ny*nx, host). */
+int lbm_batch_read_density(lbm_batch *b, int i, double *rho_host);
+
+/* Radial density profiles of every instance, host array [n][nb]: at s_k =
+ * (k + 1/2) smax/nb the mean over 64 directions of the bilinearly interpolated
+ * density at distance s R from the lattice centre (droplet, bubble), or the mean
+ * over x and both sides at y = ny/2 +- s h (slab). */
+int lbm_batch_profiles(lbm_batch *b, int nb, double smax, double *prof_host);
+
+/* Tile shape of the batched step: row stages per warp (3 or 4) and rows per
+ * work item; lbm_batch_autotune times the candidates (stages 3, 4 x rows 32,
+ * 64, 128, 256) for trial_steps steps each without advancing the state and
+ * keeps the fastest. */
+int lbm_batch_set_tuning(lbm_batch *b, int stages, int rows_per_item);
+int lbm_batch_autotune(lbm_batch *b, int trial_steps, int *stages, int *rows_per_item, double *ms_per_step);
+
+/* Total lattice nodes of the batch (-1 if b is NULL). */
+int64_t lbm_batch_nodes(lbm_batch *b);
+
+/* ---- learned warm start ----
+ * The paper has no learned component; this network serves the batched
+ * solver.  A tanh multilayer perceptron n_in -> n_hidden (x hidden_layers) ->
+ * n_out, FP32, trained and evaluated by the library's own CUDA kernels
+ * (forward, backward, Adam).  For the warm start the inputs are (T/Tc, tau,
+ * A, K, radius) and the outputs log-density samples of the converged profile
+ * (see lbm_batch_profiles).  Inputs and targets are standardised inside the
+ * model with the affine scalings of lbm_ws_set_scaling.  Parameters are
+ * flattened layer by layer as [W (out x in, row-major), b], hidden layers
+ * first.  Host arrays are row-major [n][n_in] / [n][n_out] floats; all calls
+ * synchronise. */
+typedef struct {
+    int32_t n_in, n_hidden, hidden_layers, n_out;
+    uint64_t seed;      /* Glorot-uniform initial weights from SplitMix64(seed) */
+} lbm_ws_cfg;
+
+typedef struct lbm_ws lbm_ws;
+
+int lbm_ws_create(const lbm_ws_cfg *cfg, lbm_ws **out);
+void lbm_ws_destroy(lbm_ws *w);
+int lbm_ws_num_params(lbm_ws *w, int64_t *n);
+int lbm_ws_set_scaling(lbm_ws *w, const float *x_mean, const float *x_std, const float *y_mean, const float *y_std);
+int lbm_ws_get_params(lbm_ws *w, float *params_host);
+int lbm_ws_set_params(lbm_ws *w, const float *params_host);   /* also resets the Adam state */
+
+/* Mean squared error in standardised output units over n samples and its
+ * gradient with respect to the flattened parameters (grad_host may be NULL). */
+int lbm_ws_loss_grad(lbm_ws *w, const float *X_host, const float *Y_host, int n, float *loss, float *grad_host);
+
+/* Adam (beta1 0.9, beta2 0.999, eps 1e-8) on minibatches of the MSE, epochs
+ * passes over a per-epoch SplitMix64(seed) shuffle; final_loss (may be NULL)
+ * receives the loss over all n samples afterwards. */
+int lbm_ws_train(lbm_ws *w, const float *X_host, const float *Y_host, int n, int epochs, int batch, float lr,
+                 uint64_t seed, float *final_loss);
+
+/* Network outputs (in target units) for n input rows. */
+int lbm_ws_predict(lbm_ws *w, const float *X_host, int n, float *Y_host);
+
 /* ---- observables without allocation ----
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory: code inside a host application whose memory

@@ -152,22 +152,28 @@ int status_code(unsigned bits)
     if (bits & ST_NONFINITE) return LBM_E_NONFINITE;
     if (bits & ST_EOS) return LBM_E_EOS_DOMAIN;
     if (bits & ST_TIMEOUT) return LBM_E_TIMEOUT;
+    if (bits & ST_ALIGN) return LBM_E_CUDA;
     return LBM_OK;
+}
+
+// The deviation reference exactly as the kernels see it (rounded to float on
+// the FP32 path), so that stored deviations and rho = rho_ref + sum g agree.
+double rho_ref_eff(const lbm_params& p)
+{
+    return p.precision == LBM_FP64 ? 0.0 : double(float(p.rho_ref));
 }
 
 template <typename T>
 void launch_init_rest(lbm_ctx* c, const double* rho0)
 {
-    k_init_rest<T><<<1024, 256, 0, c->stream>>>(rho0, (T*)c->f[c->cur], c->p.nx, c->p.ny,
-                                                  c->p.precision == LBM_FP64 ? 0.0 : c->p.rho_ref);
+    k_init_rest<T><<<1024, 256, 0, c->stream>>>(rho0, (T*)c->f[c->cur], c->p.nx, c->p.ny, rho_ref_eff(c->p));
 }
 
 template <typename T>
 void launch_plane(lbm_ctx* c, int a, int to_stored)
 {
     k_plane_convert<T><<<1024, 256, 0, c->stream>>>((T*)c->f[c->cur], c->rho, a, c->p.nx, c->p.ny,
-                                                      c->p.precision == LBM_FP64 ? 0.0 : c->p.rho_ref,
-                                                      to_stored);
+                                                      rho_ref_eff(c->p), to_stored);
 }
 
 int reset_state(lbm_ctx* c)

@@ -13,7 +13,7 @@ namespace lbm {
 
 enum : int { BGK = 0, MRT = 1 };
 enum : int { GUO = 0, EDM = 1, SC = 2 };
-enum : unsigned { ST_NONFINITE = 1u, ST_EOS = 2u, ST_TIMEOUT = 4u };
+enum : unsigned { ST_NONFINITE = 1u, ST_EOS = 2u, ST_TIMEOUT = 4u, ST_ALIGN = 8u };
 
 // D2Q9 velocities (Sec. 2): 0 rest, 1-4 axes, 5-8 diagonals.
 __host__ __device__ constexpr int ex(int a) { return a == 1 || a == 5 || a == 8 ? 1 : (a == 3 || a == 6 || a == 7 ? -1 : 0); }
@@ -26,7 +26,8 @@ __host__ __device__ constexpr C wt(int a) { return a == 0 ? C(4) / C(9) : (a < 5
 // path's tolerances), IEEE operations for double.
 __device__ __forceinline__ float cdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double cdiv(double a, double b) { return a / b; }
-__device__ __forceinline__ float csqrt(float a) { return sqrtf(a); }
+// Square root of a >= 0 (0 maps to 0).
+__device__ __forceinline__ float csqrt(float a) { return a > 0.f ? a * rsqrtf(a) : 0.f; }
 __device__ __forceinline__ double csqrt(double a) { return sqrt(a); }
 
 // Per-lattice constants in the compute type.
@@ -41,6 +42,11 @@ struct Coef {
     C guo_pre;    // 1 - 1/(2 tau)  (Eq. 23)
     C s_e, s_eps, s_q;  // MRT rates (Eq. 35); s_nu = omega
     C rho_ref;    // deviation reference (0 for FP64)
+    // MRT relaxation of moment m with rate s, equilibrium m^eq and source S,
+    // already divided by the squared norm n of its row of M (M^-1 = M^T / n):
+    //   (m - s (m - m^eq) + (1 - s/2) S) / n = r0 m + r1 m^eq + r2 S
+    // rows: 0 = e (s_e, n 36), 1 = eps (s_eps, 36), 2 = q (s_q, 12), 3 = nu (1/tau, 4)
+    C r0[4], r1[4], r2[4];
 };
 
 // psi from the K-scaled Carnahan-Starling EOS (Eqs. 29-30, a = 1, b = 4,
@@ -67,18 +73,20 @@ __device__ __forceinline__ C psi_of_rho(C rho, const Coef<C>& k, unsigned& bad)
 template <typename C>
 struct Stencil { C c, e, n, w, s, ne, nw, sw, se; };
 
+// Both terms share the neighbour sum, so F = sum_a w_a e_a phi(x+e_a) with
+// phi(n) = psi(n) [(A/2) psi(n) + (1 - A) psi(x)].
 template <typename C>
 __device__ __forceinline__ void force(const Stencil<C>& q, const Coef<C>& k, C& Fx, C& Fy)
 {
     const C w1 = C(1) / C(3), w2 = C(1) / C(12);
-    const C sx1 = w1 * (q.e - q.w) + w2 * ((q.ne - q.sw) + (q.se - q.nw));
-    const C sy1 = w1 * (q.n - q.s) + w2 * ((q.ne - q.sw) + (q.nw - q.se));
-    const C e2 = q.e * q.e, w2s = q.w * q.w, n2 = q.n * q.n, s2 = q.s * q.s;
-    const C ne2 = q.ne * q.ne, nw2 = q.nw * q.nw, sw2 = q.sw * q.sw, se2 = q.se * q.se;
-    const C sx2 = w1 * (e2 - w2s) + w2 * ((ne2 - sw2) + (se2 - nw2));
-    const C sy2 = w1 * (n2 - s2) + w2 * ((ne2 - sw2) + (nw2 - se2));
-    Fx = k.half_A * sx2 + k.one_m_A * q.c * sx1;
-    Fy = k.half_A * sy2 + k.one_m_A * q.c * sy1;
+    const C cc = k.one_m_A * q.c;
+    const C pe = q.e * (k.half_A * q.e + cc), pw = q.w * (k.half_A * q.w + cc);
+    const C pn = q.n * (k.half_A * q.n + cc), ps = q.s * (k.half_A * q.s + cc);
+    const C pne = q.ne * (k.half_A * q.ne + cc), psw = q.sw * (k.half_A * q.sw + cc);
+    const C pse = q.se * (k.half_A * q.se + cc), pnw = q.nw * (k.half_A * q.nw + cc);
+    const C d1 = pne - psw, d2 = pse - pnw;
+    Fx = w1 * (pe - pw) + w2 * (d1 + d2);
+    Fy = w1 * (pn - ps) + w2 * (d1 - d2);
 }
 
 // Moments of the deviations (Eq. 3): drho = sum g (rho = rho_ref + drho),
@@ -152,52 +160,41 @@ __device__ __forceinline__ void collide(C g[9], C Fx, C Fy, const Coef<C>& k, C&
     } else {
         static_assert(COLL == MRT && FORC == GUO, "MRT supports Guo forcing only");
         // Eq. 34 in the orthogonal D2Q9 moment basis (rho, e, eps, jx, qx, jy,
-        // qy, pxx, pxy), with m, m^eq and S = M (Guo source / (1 - 1/2tau)) in
-        // closed form.  Deviations shift m by -rho_ref (1, -2, 1, 0, ..., 0).
-        const C m1 = -C(4) * g[0] - ((g[1] + g[3]) + (g[2] + g[4])) + C(2) * ((g[5] + g[7]) + (g[6] + g[8]));
-        const C m2 = C(4) * g[0] - C(2) * ((g[1] + g[3]) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]));
-        const C m4 = -C(2) * (g[1] - g[3]) + ((g[5] - g[7]) + (g[8] - g[6]));
-        const C m6 = -C(2) * (g[2] - g[4]) + ((g[5] - g[7]) + (g[6] - g[8]));
-        const C m7 = (g[1] + g[3]) - (g[2] + g[4]);
-        const C m8 = (g[5] + g[7]) - (g[6] + g[8]);
-        const C v2 = vx * vx + vy * vy;
-        const C rv2 = C(3) * rho * v2;
-        const C eq1 = -C(2) * drho + rv2;        // rho(-2 + 3v^2) + 2 rho_ref
-        const C eq2 = drho - rv2;                // rho(1 - 3v^2) - rho_ref
-        const C eq4 = -rho * vx, eq6 = -rho * vy;
-        const C eq7 = rho * (vx * vx - vy * vy), eq8 = rho * vx * vy;
-        const C vF = vx * Fx + vy * Fy;
-        const C S1 = C(6) * vF, S2 = -C(6) * vF, S4 = -Fx, S6 = -Fy;
-        const C S7 = C(2) * (vx * Fx - vy * Fy), S8 = vx * Fy + vy * Fx;
-        const C s_nu = k.omega;
-        // m* = m - s (m - m^eq) + (1 - s/2) S; rho and j come out as drho, j + F.
-        const C a0 = drho;
-        const C a1 = m1 - k.s_e * (m1 - eq1) + (C(1) - C(0.5) * k.s_e) * S1;
-        const C a2 = m2 - k.s_eps * (m2 - eq2) + (C(1) - C(0.5) * k.s_eps) * S2;
-        const C a3 = jx + Fx;
-        const C a4 = m4 - k.s_q * (m4 - eq4) + (C(1) - C(0.5) * k.s_q) * S4;
-        const C a5 = jy + Fy;
-        const C a6 = m6 - k.s_q * (m6 - eq6) + (C(1) - C(0.5) * k.s_q) * S6;
-        const C a7 = m7 - s_nu * (m7 - eq7) + (C(1) - C(0.5) * s_nu) * S7;
-        const C a8 = m8 - s_nu * (m8 - eq8) + (C(1) - C(0.5) * s_nu) * S8;
-        // f* = M^-1 m* with M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).
-        const C b0 = a0 * (C(1) / C(9)), b1 = a1 * (C(1) / C(36)), b2 = a2 * (C(1) / C(36));
-        const C b3 = a3 * (C(1) / C(6)), b4 = a4 * (C(1) / C(12));
-        const C b5 = a5 * (C(1) / C(6)), b6 = a6 * (C(1) / C(12));
-        const C b7 = a7 * C(0.25), b8 = a8 * C(0.25);
-        const C axis = b0 - b1 - C(2) * b2;      // common part of e1..e4
-        const C diag = b0 + C(2) * b1 + b2;      // common part of e5..e8
+        // qy, pxx, pxy) with m, m^eq and S = M (Guo source / (1 - 1/2tau)) in
+        // closed form; each relaxed moment comes out already scaled by 1/n of
+        // its row, ready for f* = M^T (m* / n).  Deviations shift m by
+        // -rho_ref (1, -2, 1, 0, ..., 0), which the equilibria absorb.
+        const C Sa = g[1] + g[3], Sb = g[2] + g[4], Sc = g[5] + g[7], Sd = g[6] + g[8];
+        const C axis = Sa + Sb, diag = Sc + Sd;
+        const C D1 = g[1] - g[3], D2 = g[2] - g[4], D57 = g[5] - g[7], D86 = g[8] - g[6];
+        const C m1 = C(2) * diag - axis - C(4) * g[0];
+        const C m2 = diag - C(2) * axis + C(4) * g[0];
+        const C m4 = (D57 + D86) - C(2) * D1;
+        const C m6 = (D57 - D86) - C(2) * D2;
+        const C m7 = Sa - Sb, m8 = Sc - Sd;
+        const C vx2 = vx * vx, vy2 = vy * vy;
+        const C rv2 = C(3) * rho * (vx2 + vy2);
+        const C vF6 = C(6) * (vx * Fx + vy * Fy);
+        const C b1 = k.r0[0] * m1 + k.r1[0] * (rv2 - C(2) * drho) + k.r2[0] * vF6;
+        const C b2 = k.r0[1] * m2 + k.r1[1] * (drho - rv2) - k.r2[1] * vF6;
+        const C b4 = k.r0[2] * m4 - k.r1[2] * (rho * vx) - k.r2[2] * Fx;
+        const C b6 = k.r0[2] * m6 - k.r1[2] * (rho * vy) - k.r2[2] * Fy;
+        const C b7 = k.r0[3] * m7 + k.r1[3] * (rho * (vx2 - vy2)) + k.r2[3] * (C(2) * (vx * Fx - vy * Fy));
+        const C b8 = k.r0[3] * m8 + k.r1[3] * (rho * vx * vy) + k.r2[3] * (vx * Fy + vy * Fx);
+        const C b0 = drho * (C(1) / C(9));
+        const C b3 = (jx + Fx) * (C(1) / C(6)), b5 = (jy + Fy) * (C(1) / C(6));
+        const C ax = b0 - b1 - C(2) * b2;      // common part of e1..e4
+        const C dg = b0 + C(2) * b1 + b2;      // common part of e5..e8
         const C px = b3 - C(2) * b4, py = b5 - C(2) * b6;
         const C dx = b3 + b4, dy = b5 + b6;
-        g[0] = b0 - C(4) * b1 + C(4) * b2;
-        g[1] = axis + px + b7;
-        g[3] = axis - px + b7;
-        g[2] = axis + py - b7;
-        g[4] = axis - py - b7;
-        g[5] = diag + dx + dy + b8;
-        g[6] = diag - dx + dy - b8;
-        g[7] = diag - dx - dy + b8;
-        g[8] = diag + dx - dy - b8;
+        g[1] = ax + px + b7;
+        g[3] = ax - px + b7;
+        g[2] = ax + py - b7;
+        g[4] = ax - py - b7;
+        g[5] = dg + (dx + dy) + b8;
+        g[7] = dg - (dx + dy) + b8;
+        g[6] = dg - (dx - dy) - b8;
+        g[8] = dg + (dx - dy) - b8;
     }
     // Every scheme conserves mass (sum f* = rho).  Close the rest population
     // on it so that rounding in the equilibrium weights (4/9, 1/9, 1/36 and

@@ -24,7 +24,7 @@ int lbm_preset_field(int nx, int ny, int kind, double size, double width, double
 
 // Pipelined strip kernel (lbm_strip*.cu): whether it supports p, its tuning
 // configurations (threads per CTA, row stages), and one step with one of them.
-struct StripConfig { int threads, stages; };
+struct StripConfig { int threads, stages, warp; };
 bool lbm_strip_supported(const lbm_params* p);
 int lbm_strip_config_count(int precision);
 StripConfig lbm_strip_config(int precision, int cfg);
@@ -47,6 +47,13 @@ lbm::Coef<C> make_coef(const lbm_params& p)
     k.s_eps = C(p.s_eps);
     k.s_q = C(p.s_q);
     k.rho_ref = C(p.precision == LBM_FP64 ? 0.0 : p.rho_ref);
+    const double rate[4] = {p.s_e, p.s_eps, p.s_q, 1.0 / p.tau};
+    const double norm[4] = {36.0, 36.0, 12.0, 4.0};
+    for (int i = 0; i < 4; ++i) {
+        k.r0[i] = C((1.0 - rate[i]) / norm[i]);
+        k.r1[i] = C(rate[i] / norm[i]);
+        k.r2[i] = C((1.0 - 0.5 * rate[i]) / norm[i]);
+    }
     return k;
 }
 #endif  // __CUDACC__

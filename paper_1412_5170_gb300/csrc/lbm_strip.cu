@@ -22,7 +22,7 @@ int lbm_strip_config_count(int precision)
 StripConfig lbm_strip_config(int precision, int cfg)
 {
     const int n = lbm_strip_config_count(precision);
-    if (cfg < 0 || cfg >= n) return StripConfig{0, 0};
+    if (cfg < 0 || cfg >= n) return StripConfig{0, 0, 0};
     return precision == LBM_FP64 ? kStripF64[cfg] : kStripF32[cfg];
 }
 

@@ -71,6 +71,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
                  ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
 
+// Alignment the staged kernels rely on: 128 bytes for the dynamic shared
+// memory base (bulk-copy destinations, 128-bit shared loads, mbarriers) and
+// 16 bytes for the population buffers (bulk-copy sources, 128-bit stores).
+// A CTA that finds either violated flags ST_ALIGN and does no memory access.
+__device__ __forceinline__ bool staged_alignment_ok(const void* smem, const void* fin, const void* fout)
+{
+    return (((uintptr_t)__cvta_generic_to_shared(smem) & 127u) == 0) &&
+           ((((uintptr_t)fin | (uintptr_t)fout) & 15u) == 0);
+}
+
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
@@ -136,43 +146,62 @@ __device__ __forceinline__ C drho1(const T* __restrict__ st, int stride, int c)
     return sum9(s);
 }
 
-template <typename T, typename C, int COLL, int FORC, int NT, int NS>
-__global__ void __launch_bounds__(NT)
-k_step_strip(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, int nchunks, Coef<C> k,
-             unsigned* __restrict__ status)
+// Shared-memory carve-up of a strip CTA: NS stages [9][W+8] of T, a 4-row psi
+// ring [4][W+8] of C, NS mbarriers.
+template <typename T, typename C, int NT, int NS>
+struct StripSmem {
+    static constexpr int W = 4 * NT;
+    static constexpr int SW = W + 8;     // stage row stride (elements)
+    static constexpr int PW = W + 8;     // psi ring row stride: column c at index 4 + c
+    T* stages;
+    C* psi;
+    uint64_t* bars;
+    __device__ explicit StripSmem(unsigned char* smem)
+        : stages(reinterpret_cast<T*>(smem)),
+          psi(reinterpret_cast<C*>(smem + sizeof(T) * NS * 9 * SW)),
+          bars(reinterpret_cast<uint64_t*>(smem + sizeof(T) * NS * 9 * SW + sizeof(C) * 4 * PW)) {}
+};
+
+template <typename T, typename C, int NT, int NS>
+__device__ __forceinline__ void strip_init_barriers(const StripSmem<T, C, NT, NS>& sm)
 {
-    constexpr int W = 4 * NT;
-    constexpr int SW = W + 8;            // stage row stride (elements)
-    constexpr int PW = W + 8;            // psi ring row stride: column c at index 4 + c
-    extern __shared__ __align__(128) unsigned char smem[];
-    T* stages = reinterpret_cast<T*>(smem);                                  // [NS][9][SW]
-    C* psi = reinterpret_cast<C*>(smem + sizeof(T) * NS * 9 * SW);           // [4][PW]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + sizeof(T) * NS * 9 * SW + sizeof(C) * 4 * PW);
-
-    const int t = threadIdx.x;
-    const int x0 = blockIdx.x * W;
-    const int wp = min(W, nx - x0);                         // strip width (multiple of 4)
-    const int y0 = int((long long)blockIdx.y * ny / nchunks);
-    const int y1 = int((long long)(blockIdx.y + 1) * ny / nchunks);
-    const int H = y1 - y0;
-    if (H <= 0) return;
-    const size_t n = (size_t)nx * ny;
-    const int nrows = H + 2;                                // walk rows incl. 2 halo rows
-    const unsigned stage_bytes = unsigned(9 * (wp + 8) * sizeof(T));
-    const bool left_wrap = x0 == 0, right_wrap = x0 + wp == nx;
-
-    if (t == 0) {
-        for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) mbar_init(&sm.bars[s], 1);
         fence_mbar_init();
     }
     __syncthreads();
+}
+
+// Walk one strip segment: columns [x0, x0 + min(W, nx - x0)), rows [y0, y1).
+// G counts walk rows over every segment this CTA has walked: row G uses
+// stage G % NS in its (G / NS)-th phase, so segments can follow one another
+// without re-initialising the barriers.  Returns false (with ST_TIMEOUT in
+// bad) if a stage wait gave up; the copies already issued are then drained
+// (bounded) and the CTA must stop.  All threads of the CTA call this with
+// the same arguments.
+template <typename T, typename C, int COLL, int FORC, int NT, int NS>
+__device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny,
+                                           int x0, int y0, int y1, const Coef<C>& k,
+                                           const StripSmem<T, C, NT, NS>& sm, unsigned& G, unsigned& bad)
+{
+    using SM = StripSmem<T, C, NT, NS>;
+    constexpr int SW = SM::SW, PW = SM::PW;
+    const int t = threadIdx.x;
+    const int wp = min(SM::W, nx - x0);                      // strip width (multiple of 4)
+    const int H = y1 - y0;
+    const size_t n = (size_t)nx * ny;
+    const int nrows = H + 2;                                 // walk rows incl. 2 halo rows
+    const unsigned stage_bytes = unsigned(9 * (wp + 8) * sizeof(T));
+    const bool left_wrap = x0 == 0, right_wrap = x0 + wp == nx;
+    const unsigned base = G;
 
     // Warp 0 issues the nine segment copies of walk row kr into its stage.
     auto issue = [&](int kr) {
         if (t >= 32) return;
-        const int slot = kr % NS;
-        T* st = stages + slot * 9 * SW;
-        if (t == 0) mbar_arrive_expect_tx(&bars[slot], stage_bytes);
+        const unsigned g = base + kr;
+        uint64_t* bar = &sm.bars[g % NS];
+        T* st = sm.stages + (g % NS) * 9 * SW;
+        if (t == 0) mbar_arrive_expect_tx(bar, stage_bytes);
         __syncwarp();
         if (t < 9) {
             fence_proxy_async();   // order earlier generic reads of this slot before the async writes
@@ -181,38 +210,38 @@ k_step_strip(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, in
             const T* row = fin + a * n + (size_t)r * nx;
             T* dst = st + a * SW;
             if (!left_wrap && !right_wrap) {
-                bulk_g2s(dst, row + x0 - 4, unsigned((wp + 8) * sizeof(T)), &bars[slot]);
+                bulk_g2s(dst, row + x0 - 4, unsigned((wp + 8) * sizeof(T)), bar);
             } else {
-                bulk_g2s(dst, row + (left_wrap ? nx - 4 : x0 - 4), unsigned(4 * sizeof(T)), &bars[slot]);
-                bulk_g2s(dst + 4, row + x0, unsigned(wp * sizeof(T)), &bars[slot]);
-                bulk_g2s(dst + 4 + wp, row + (right_wrap ? 0 : x0 + wp), unsigned(4 * sizeof(T)), &bars[slot]);
+                bulk_g2s(dst, row + (left_wrap ? nx - 4 : x0 - 4), unsigned(4 * sizeof(T)), bar);
+                bulk_g2s(dst + 4, row + x0, unsigned(wp * sizeof(T)), bar);
+                bulk_g2s(dst + 4 + wp, row + (right_wrap ? 0 : x0 + wp), unsigned(4 * sizeof(T)), bar);
             }
         }
     };
 
     for (int kr = 0; kr < NS - 2 && kr < nrows; ++kr) issue(kr);
 
-    unsigned bad = 0;
     const int c0 = 4 * t;
     const bool active = c0 < wp;
     int kdone = 0;                         // walk rows whose stage wait completed
+    bool ok_all = true;
     for (int kk = 0; kk < nrows; ++kk) {
-        const int slot = kk % NS;
-        const T* st = stages + slot * 9 * SW;
-        const bool ok = mbar_wait(&bars[slot], (kk / NS) & 1);
+        const unsigned g = base + kk;
+        const T* st = sm.stages + (g % NS) * 9 * SW;
+        const bool ok = mbar_wait(&sm.bars[g % NS], (g / NS) & 1);
         // psi of walk row kk
-        C* prow = psi + (kk & 3) * PW;
+        C* prow = sm.psi + (kk & 3) * PW;
         if (ok) {
             if (active) {
-                C g[9][4];
-                pull4<T, C>(st, SW, c0, g);
+                C gv[9][4];
+                pull4<T, C>(st, SW, c0, gv);
                 C ps[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    C s[9];
+                    C s9[9];
 #pragma unroll
-                    for (int a = 0; a < 9; ++a) s[a] = g[a][j];
-                    ps[j] = psi_of_rho<C>(k.rho_ref + sum9(s), k, bad);
+                    for (int a = 0; a < 9; ++a) s9[a] = gv[a][j];
+                    ps[j] = psi_of_rho<C>(k.rho_ref + sum9(s9), k, bad);
                 }
                 sts4(prow + 4 + c0, ps);
             }
@@ -222,6 +251,7 @@ k_step_strip(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, in
         if (__syncthreads_or(!ok)) {
             bad |= ST_TIMEOUT;
             kdone = kk;
+            ok_all = false;
             break;
         }
         kdone = kk + 1;
@@ -230,12 +260,12 @@ k_step_strip(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, in
         // collide walk row kk-1 (a chunk row when 1 <= kk-1 <= H)
         const int kc = kk - 1;
         if (kc >= 1 && kc <= H && active) {
-            const T* sc = stages + (kc % NS) * 9 * SW;
-            C g[9][4];
-            pull4<T, C>(sc, SW, c0, g);
-            const C* pm = psi + ((kc - 1) & 3) * PW + 4 + c0;   // row y - 1
-            const C* p0 = psi + (kc & 3) * PW + 4 + c0;         // row y
-            const C* pp = psi + ((kc + 1) & 3) * PW + 4 + c0;   // row y + 1
+            const T* sc = sm.stages + ((base + kc) % NS) * 9 * SW;
+            C gv[9][4];
+            pull4<T, C>(sc, SW, c0, gv);
+            const C* pm = sm.psi + ((kc - 1) & 3) * PW + 4 + c0;   // row y - 1
+            const C* p0 = sm.psi + (kc & 3) * PW + 4 + c0;         // row y
+            const C* pp = sm.psi + ((kc + 1) & 3) * PW + 4 + c0;   // row y + 1
             C rm[6], r0[6], rp[6];     // columns c0-1 .. c0+4
             {
                 C v[4];
@@ -250,26 +280,51 @@ k_step_strip(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, in
                 C Fx, Fy, vx, vy, rho, gj[9];
                 force<C>(q, k, Fx, Fy);
 #pragma unroll
-                for (int a = 0; a < 9; ++a) gj[a] = g[a][j];
+                for (int a = 0; a < 9; ++a) gj[a] = gv[a][j];
                 collide<C, COLL, FORC>(gj, Fx, Fy, k, vx, vy, rho);
                 bad |= finite_bits<C>(gj);
 #pragma unroll
-                for (int a = 0; a < 9; ++a) g[a][j] = gj[a];
+                for (int a = 0; a < 9; ++a) gv[a][j] = gj[a];
             }
             const int y = y0 + kc - 1;
             T* out = fout + (size_t)y * nx + x0 + c0;
 #pragma unroll
-            for (int a = 0; a < 9; ++a) stg4(out + a * n, T(g[a][0]), T(g[a][1]), T(g[a][2]), T(g[a][3]));
+            for (int a = 0; a < 9; ++a) stg4(out + a * n, T(gv[a][0]), T(gv[a][1]), T(gv[a][2]), T(gv[a][3]));
         }
     }
-    if (bad & ST_TIMEOUT) {
+    if (!ok_all) {
         // Drain copies already issued for rows the walk never consumed (bounded).
         if (t == 0) {
             const int issued = min(nrows, kdone + NS - 2);
-            for (int kr = kdone; kr < issued; ++kr) mbar_wait(&bars[kr % NS], (kr / NS) & 1);
+            for (int kr = kdone; kr < issued; ++kr) mbar_wait(&sm.bars[(base + kr) % NS], ((base + kr) / NS) & 1);
         }
         __syncthreads();
+        return false;
     }
+    G = base + nrows;
+    __syncthreads();   // every read of this segment's stages is done before the next segment's copies
+    return true;
+}
+
+// One lattice, grid (strips, row chunks).
+template <typename T, typename C, int COLL, int FORC, int NT, int NS>
+__global__ void __launch_bounds__(NT)
+k_step_strip(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, int nchunks, Coef<C> k,
+             unsigned* __restrict__ status)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (!staged_alignment_ok(smem, fin, fout)) {
+        if (threadIdx.x == 0) atomicOr(status, ST_ALIGN);
+        return;
+    }
+    const StripSmem<T, C, NT, NS> sm(smem);
+    const int x0 = blockIdx.x * (4 * NT);
+    const int y0 = int((long long)blockIdx.y * ny / nchunks);
+    const int y1 = int((long long)(blockIdx.y + 1) * ny / nchunks);
+    if (y1 <= y0) return;
+    strip_init_barriers(sm);
+    unsigned G = 0, bad = 0;
+    strip_walk<T, C, COLL, FORC, NT, NS>(fin, fout, nx, ny, x0, y0, y1, k, sm, G, bad);
     flag_status(bad, status);
 }
 

@@ -4,7 +4,7 @@
 
 using namespace lbm;
 
-extern const StripConfig kStripF64[] = {{64, 4}, {32, 6}, {64, 3}};
+extern const StripConfig kStripF64[] = {{64, 4, 0}, {32, 6, 0}, {64, 3, 0}};
 extern const int kStripF64Count = sizeof(kStripF64) / sizeof(kStripF64[0]);
 
 int lbm_strip_launch_f64(const lbm_params* p, int cfg, const void* fin, void* fout, unsigned* st, cudaStream_t s)

@@ -50,6 +50,30 @@ class lbm_stats_t(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class lbm_batch_params(ctypes.Structure):
+    _fields_ = [("collision", ctypes.c_int32), ("forcing", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double),
+                ("s_q", ctypes.c_double)]
+
+
+class lbm_instance(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("kind", ctypes.c_int32), ("cell", ctypes.c_int32),
+                ("T_over_Tc", ctypes.c_double), ("tau", ctypes.c_double), ("A", ctypes.c_double),
+                ("K", ctypes.c_double), ("size", ctypes.c_double), ("width", ctypes.c_double),
+                ("rho_l", ctypes.c_double), ("rho_v", ctypes.c_double), ("noise_amp", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
+class lbm_ws_cfg(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_int32), ("n_hidden", ctypes.c_int32), ("hidden_layers", ctypes.c_int32),
+                ("n_out", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+BATCH_NOBS = 10
+BATCH_OBS = ("mass", "max_v", "max_dv", "max_drho", "rho_min", "rho_max", "rho_center", "rho_corner",
+             "rho_row_mid", "rho_row0")
+RUNNING, CONVERGED, FAILED = 0, 1, 2
+
 _vp, _dp, _i64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64
 _PROTOS = {
     "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -79,6 +103,31 @@ _PROTOS = {
     "lbm_get_config": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "lbm_set_config": (ctypes.c_int, [_vp, ctypes.c_int]),
     "lbm_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp]),
+    "lbm_batch_create": (ctypes.c_int, [ctypes.POINTER(lbm_batch_params), ctypes.POINTER(lbm_instance), ctypes.c_int,
+                                        ctypes.POINTER(_vp)]),
+    "lbm_batch_destroy": (None, [_vp]),
+    "lbm_batch_init": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double]),
+    "lbm_batch_step": (ctypes.c_int, [_vp, _i64]),
+    "lbm_batch_run_to_steady": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _i64, _i64,
+                                               ctypes.POINTER(_i64)]),
+    "lbm_batch_observe": (ctypes.c_int, [_vp]),
+    "lbm_batch_results": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "lbm_batch_read_density": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "lbm_batch_profiles": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, _vp]),
+    "lbm_batch_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "lbm_batch_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int), _dp]),
+    "lbm_batch_nodes": (ctypes.c_int64, [_vp]),
+    "lbm_ws_create": (ctypes.c_int, [ctypes.POINTER(lbm_ws_cfg), ctypes.POINTER(_vp)]),
+    "lbm_ws_destroy": (None, [_vp]),
+    "lbm_ws_num_params": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
+    "lbm_ws_set_scaling": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "lbm_ws_get_params": (ctypes.c_int, [_vp, _vp]),
+    "lbm_ws_set_params": (ctypes.c_int, [_vp, _vp]),
+    "lbm_ws_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float), _vp]),
+    "lbm_ws_train": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                    ctypes.c_uint64, ctypes.POINTER(ctypes.c_float)]),
+    "lbm_ws_predict": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp]),
 }
 for _name, (_res, _args) in _PROTOS.items():
     _f = getattr(_lib, _name)
@@ -256,3 +305,168 @@ class Lattice:
     @variant.setter
     def variant(self, v: int):
         check(lbm_set_variant(self.ctx, int(v)), "lbm_set_variant")
+
+
+class Batch:
+    """Many independent lattices advanced together (FP32 deviations).
+
+    instances: list of dicts with keys nx, ny (or side), kind, T_over_Tc, tau,
+    A, K, size and optional width (4), rho_l / rho_v (0: Maxwell), cell, seed,
+    noise_amp (1e-6)."""
+
+    def __init__(self, instances, collision="bgk", forcing="guo", s_e=0.8, s_eps=0.8, s_q=1.1):
+        bp = lbm_batch_params(COLLISION[collision], FORCING[forcing], FP32_DEV, 0, float(s_e), float(s_eps),
+                              float(s_q))
+        arr = (lbm_instance * len(instances))()
+        for i, d in enumerate(instances):
+            nx = int(d.get("nx", d.get("side")))
+            ny = int(d.get("ny", d.get("side")))
+            kind = d.get("kind", "droplet")
+            arr[i] = lbm_instance(nx, ny, PRESET[kind] if isinstance(kind, str) else int(kind), int(d.get("cell", 256)),
+                                  float(d["T_over_Tc"]), float(d["tau"]), float(d["A"]), float(d.get("K", 1.0)),
+                                  float(d["size"]), float(d.get("width", 4.0)), float(d.get("rho_l", 0.0)),
+                                  float(d.get("rho_v", 0.0)), float(d.get("noise_amp", 1e-6)),
+                                  int(d.get("seed", 0)) & (2 ** 64 - 1))
+        self.n = len(instances)
+        self.shapes = [(arr[i].ny, arr[i].nx) for i in range(self.n)]
+        h = _vp()
+        check(lbm_batch_create(ctypes.byref(bp), arr, self.n, ctypes.byref(h)), "lbm_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def nodes(self) -> int:
+        return int(lbm_batch_nodes(self.h))
+
+    def init(self, profiles=None, use=None, smax=2.0):
+        """Presets, or (with a torch CUDA float64 tensor profiles [n, nb] and a
+        0/1 sequence use) density profiles for the selected instances."""
+        if profiles is None:
+            check(lbm_batch_init(self.h, None, None, 0, 0.0), "lbm_batch_init")
+            return
+        nb = int(profiles.shape[1])
+        on = (ctypes.c_int32 * self.n)(*[int(bool(u)) for u in use])
+        check(lbm_batch_init(self.h, _vp(profiles.data_ptr()), on, nb, float(smax)), "lbm_batch_init")
+
+    def step(self, n: int):
+        check(lbm_batch_step(self.h, int(n)), "lbm_batch_step")
+
+    def run_to_steady(self, tol_v=0.0, tol_rho=0.0, check_every=1000, max_steps=10 ** 6):
+        done = _i64()
+        st = lbm_batch_run_to_steady(self.h, float(tol_v), float(tol_rho), int(check_every), int(max_steps),
+                                     ctypes.byref(done))
+        return st, done.value
+
+    def observe(self):
+        check(lbm_batch_observe(self.h), "lbm_batch_observe")
+
+    def results(self):
+        state = np.zeros(self.n, dtype=np.int32)
+        code = np.zeros(self.n, dtype=np.int32)
+        steps = np.zeros(self.n, dtype=np.int64)
+        obs = np.zeros((self.n, BATCH_NOBS))
+        check(lbm_batch_results(self.h, state.ctypes.data_as(_vp), code.ctypes.data_as(_vp),
+                                steps.ctypes.data_as(_vp), obs.ctypes.data_as(_vp)), "lbm_batch_results")
+        return state, code, steps, {k: obs[:, i] for i, k in enumerate(BATCH_OBS)}
+
+    def read_density(self, i: int) -> np.ndarray:
+        rho = np.empty(self.shapes[i])
+        check(lbm_batch_read_density(self.h, int(i), rho.ctypes.data_as(_vp)), "lbm_batch_read_density")
+        return rho
+
+    def profiles(self, nb=64, smax=2.0) -> np.ndarray:
+        out = np.empty((self.n, nb))
+        check(lbm_batch_profiles(self.h, int(nb), float(smax), out.ctypes.data_as(_vp)), "lbm_batch_profiles")
+        return out
+
+    def set_tuning(self, stages, rows):
+        check(lbm_batch_set_tuning(self.h, int(stages), int(rows)), "lbm_batch_set_tuning")
+
+    def autotune(self, trial_steps=10):
+        a, b, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        check(lbm_batch_autotune(self.h, int(trial_steps), ctypes.byref(a), ctypes.byref(b), ctypes.byref(ms)),
+              "lbm_batch_autotune")
+        return a.value, b.value, ms.value
+
+
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if shape is not None:
+        assert a.shape == shape, (a.shape, shape)
+    return a
+
+
+class WarmStartNet:
+    """The warm-start MLP (FP32, trained by liblbm's own kernels)."""
+
+    def __init__(self, n_in=5, n_hidden=128, hidden_layers=3, n_out=64, seed=0):
+        self.n_in, self.n_out = n_in, n_out
+        self.sizes = [n_in] + [n_hidden] * hidden_layers + [n_out]
+        h = _vp()
+        check(lbm_ws_create(ctypes.byref(lbm_ws_cfg(n_in, n_hidden, hidden_layers, n_out, int(seed))),
+                            ctypes.byref(h)), "lbm_ws_create")
+        self.h = h
+        n = _i64()
+        check(lbm_ws_num_params(h, ctypes.byref(n)), "lbm_ws_num_params")
+        self.n_params = n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_ws_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_scaling(self, x_mean, x_std, y_mean, y_std):
+        args = [_f32(x_mean), _f32(x_std), _f32(y_mean), _f32(y_std)]
+        check(lbm_ws_set_scaling(self.h, *[a.ctypes.data_as(_vp) for a in args]), "lbm_ws_set_scaling")
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        check(lbm_ws_get_params(self.h, out.ctypes.data_as(_vp)), "lbm_ws_get_params")
+        return out
+
+    def set_params(self, theta):
+        theta = _f32(theta, (self.n_params,))
+        check(lbm_ws_set_params(self.h, theta.ctypes.data_as(_vp)), "lbm_ws_set_params")
+
+    def loss_grad(self, X, Y):
+        X, Y = _f32(X), _f32(Y)
+        loss = ctypes.c_float()
+        g = np.empty(self.n_params, dtype=np.float32)
+        check(lbm_ws_loss_grad(self.h, X.ctypes.data_as(_vp), Y.ctypes.data_as(_vp), X.shape[0], ctypes.byref(loss),
+                               g.ctypes.data_as(_vp)), "lbm_ws_loss_grad")
+        return loss.value, g
+
+    def train(self, X, Y, epochs, batch=256, lr=1e-3, seed=0):
+        X, Y = _f32(X), _f32(Y)
+        loss = ctypes.c_float()
+        check(lbm_ws_train(self.h, X.ctypes.data_as(_vp), Y.ctypes.data_as(_vp), X.shape[0], int(epochs),
+                           int(batch), float(lr), int(seed), ctypes.byref(loss)), "lbm_ws_train")
+        return loss.value
+
+    def predict(self, X) -> np.ndarray:
+        X = _f32(X)
+        out = np.empty((X.shape[0], self.n_out), dtype=np.float32)
+        check(lbm_ws_predict(self.h, X.ctypes.data_as(_vp), X.shape[0], out.ctypes.data_as(_vp)), "lbm_ws_predict")
+        return out

@@ -1,0 +1,130 @@
+"""The batched solver (many lattices per launch, graph-captured check
+intervals, per-instance convergence and failure) against the single-lattice
+path and the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1412_5170_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def instances():
+    return [dict(side=64, kind="droplet", T_over_Tc=0.8, tau=1.0, A=-0.304, K=1.0, size=14.0, seed=1),
+            dict(nx=96, ny=40, kind="slab", T_over_Tc=0.75, tau=0.8, A=-0.304, K=0.5, size=10.0, seed=2),
+            dict(side=132, kind="droplet", T_over_Tc=0.85, tau=0.6, A=-0.304, K=0.25, size=30.0, seed=3),
+            dict(nx=260, ny=36, kind="bubble", T_over_Tc=0.8, tau=1.2, A=-0.304, K=1.0, size=12.0, seed=4)]
+
+
+@pytest.mark.parametrize("coll", ["bgk", "mrt"])
+def test_batch_matches_single_lattice_path(lbm, coll):
+    """Every instance of a batch evolves as the same lattice run alone with the
+    warp strip kernel.  The per-node arithmetic is the same; the initial fields
+    differ in the last bits (the batch evaluates the tanh preset on the device,
+    the single-lattice call on the host) and the vapour's early transient
+    amplifies that, so the bar is the FP32 element-wise bar."""
+    inst = instances()
+    with lbm.Batch(inst, collision=coll) as b:
+        b.init()
+        b.step(57)
+        got = [b.read_density(i) for i in range(len(inst))]
+    for i, d in enumerate(inst):
+        nx, ny = d.get("nx", d.get("side")), d.get("ny", d.get("side"))
+        p = lbm.make_params(nx, ny, d["T_over_Tc"], d["tau"], d["A"], d["K"], coll, "guo", "fp32",
+                            s_e=0.8, s_eps=0.8, s_q=1.1)
+        with lbm.Lattice(p) as lat:
+            lat.config = 1
+            lat.init_preset(d["kind"], d["size"], seed=d["seed"], noise_amp=1e-6)
+            lat.step(57)
+            rho, _, _ = lat.read_moments()
+        assert (np.abs(got[i] - rho) / rho).max() < 2e-5
+
+
+def test_batch_initial_field_matches_generator(lbm):
+    inst = instances()
+    with lbm.Batch(inst) as b:
+        b.init()
+        for i, d in enumerate(inst):
+            nx, ny = d.get("nx", d.get("side")), d.get("ny", d.get("side"))
+            rv, rl = lbm.maxwell(d["T_over_Tc"])
+            want = synth.density_field(nx, ny, d["kind"], rl, rv, d["size"], seed=d["seed"])
+            np.testing.assert_allclose(b.read_density(i), want, rtol=2e-7)
+
+
+def test_batch_against_oracle(lbm):
+    inst = instances()[:2]
+    steps = 120
+    with lbm.Batch(inst, collision="mrt") as b:
+        b.init()
+        b.step(steps)
+        got = [b.read_density(i) for i in range(len(inst))]
+    for i, d in enumerate(inst):
+        nx, ny = d.get("nx", d.get("side")), d.get("ny", d.get("side"))
+        rv, rl = lbm.maxwell(d["T_over_Tc"])
+        rho0 = synth.density_field(nx, ny, d["kind"], rl, rv, d["size"], seed=d["seed"])
+        q = oracle.params(nx, ny, d["T_over_Tc"], d["tau"], d["A"], d["K"], "mrt", "guo", s_e=0.8, s_eps=0.8, s_q=1.1)
+        f, _ = oracle.run(q, oracle.init_rest(rho0), steps)
+        ref = f.sum(0)
+        assert (np.abs(got[i] - ref) / ref).max() < 2e-5
+
+
+def test_run_to_steady_isolates_failures_and_converges_the_rest(lbm):
+    inst = [dict(nx=8, ny=64, kind="slab", T_over_Tc=0.85, tau=1.0, A=-0.304, K=1.0, size=16.0, seed=5),
+            dict(side=48, kind="droplet", T_over_Tc=0.5, tau=0.55, A=-0.152, K=1.0, size=12.0, seed=6),   # unstable
+            dict(nx=12, ny=64, kind="slab", T_over_Tc=0.8, tau=0.9, A=-0.304, K=0.5, size=16.0, seed=7)]
+    with lbm.Batch(inst) as b:
+        b.init()
+        st, done = b.run_to_steady(tol_rho=1e-6, check_every=500, max_steps=100000)
+        state, code, steps, obs = b.results()
+    assert st == lbm.OK
+    assert state[1] == lbm.FAILED and code[1] in (lbm.E_NONFINITE, lbm.E_EOS_DOMAIN)
+    assert state[0] == lbm.CONVERGED and state[2] == lbm.CONVERGED
+    assert obs["max_drho"][0] < 1e-6 and obs["max_drho"][2] < 1e-6
+    assert steps[1] < steps[0] or steps[1] < steps[2]
+    assert done == max(steps)
+
+
+def test_graph_intervals_equal_plain_steps(lbm):
+    inst = instances()
+    with lbm.Batch(inst) as a, lbm.Batch(inst) as c:
+        a.init()
+        c.init()
+        a.run_to_steady(tol_v=1e-30, check_every=50, max_steps=150)   # 3 graph-captured intervals
+        c.step(150)
+        for i in range(len(inst)):
+            assert np.array_equal(a.read_density(i), c.read_density(i))
+
+
+def test_profiles_of_initial_fields_and_profile_init(lbm):
+    """Radial profile of a fresh tanh droplet follows the tanh law; a field
+    built from a profile reproduces it."""
+    import torch
+    inst = [dict(side=128, kind="droplet", T_over_Tc=0.8, tau=1.0, A=-0.304, K=1.0, size=30.0, seed=8, noise_amp=0.0),
+            dict(nx=16, ny=128, kind="slab", T_over_Tc=0.8, tau=1.0, A=-0.304, K=1.0, size=25.0, seed=9, noise_amp=0.0)]
+    rv, rl = lbm.maxwell(0.8)
+    nb, smax = 64, 2.0
+    s = (np.arange(nb) + 0.5) * smax / nb
+    with lbm.Batch(inst) as b:
+        b.init()
+        prof = b.profiles(nb, smax)
+        for i, d in enumerate(inst):
+            want = rv + (rl - rv) * 0.5 * (1 - np.tanh(2 * (s * d["size"] - d["size"]) / 4.0))
+            assert np.abs(prof[i] - want).max() < 0.02 * (rl - rv)
+        dev = torch.tensor(prof, dtype=torch.float64, device="cuda")
+        b.init(dev, [1, 1], smax)
+        prof2 = b.profiles(nb, smax)
+    assert np.abs(prof2 - prof).max() < 0.02 * (rl - rv)
+
+
+def test_batch_autotune_keeps_state(lbm):
+    inst = instances()
+    with lbm.Batch(inst) as b:
+        b.init()
+        b.step(5)
+        before = [b.read_density(i) for i in range(len(inst))]
+        ns, rows, ms = b.autotune(3)
+        assert ns in (3, 4) and rows in (32, 64, 128, 256) and ms > 0
+        after = [b.read_density(i) for i in range(len(inst))]
+    for x, y in zip(before, after):
+        assert np.array_equal(x, y)
