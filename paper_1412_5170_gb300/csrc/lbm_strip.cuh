@@ -136,6 +136,48 @@ __device__ __forceinline__ void pull4(const T* __restrict__ st, int stride, int 
     }
 }
 
+// Pulled deviations of the 4 nodes [c0, c0+4) of a stage, with the +-1 column
+// neighbours of the x-shifted directions taken from the adjacent lanes by
+// shuffles; lanes with lsm (rsm) read their left (right) neighbour from the
+// stage instead (warp edges, strip edges).  Every lane of the warp must call it.
+template <typename T, typename C>
+__device__ __forceinline__ void pull4_shfl(const T* __restrict__ st, int stride, int c0, bool lsm, bool rsm,
+                                           C g[9][4])
+{
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const T* d = st + a * stride + 4 + c0;
+        T v[4];
+        lds4(d, v);
+        if (ex(a) == 0) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) g[a][j] = C(v[j]);
+        } else if (ex(a) > 0) {
+            T left = __shfl_up_sync(0xffffffffu, v[3], 1);
+            if (lsm) left = d[-1];
+            g[a][0] = C(left); g[a][1] = C(v[0]); g[a][2] = C(v[1]); g[a][3] = C(v[2]);
+        } else {
+            T right = __shfl_down_sync(0xffffffffu, v[0], 1);
+            if (rsm) right = d[4];
+            g[a][0] = C(v[1]); g[a][1] = C(v[2]); g[a][2] = C(v[3]); g[a][3] = C(right);
+        }
+    }
+}
+
+// Six psi values of one ring row around the lane's columns (c0-1 .. c0+4):
+// own four by one 128-bit load, the sides by shuffles or from shared memory.
+template <typename C>
+__device__ __forceinline__ void psi_row6(const C* __restrict__ prow, int c0, bool lsm, bool rsm, C r[6])
+{
+    C v[4];
+    lds4(prow + 4 + c0, v);
+    C left = __shfl_up_sync(0xffffffffu, v[3], 1);
+    C right = __shfl_down_sync(0xffffffffu, v[0], 1);
+    if (lsm) left = prow[3 + c0];
+    if (rsm) right = prow[8 + c0];
+    r[0] = left; r[1] = v[0]; r[2] = v[1]; r[3] = v[2]; r[4] = v[3]; r[5] = right;
+}
+
 // Pulled deviations of a single node at strip column c (c may be -1 or W).
 template <typename T, typename C>
 __device__ __forceinline__ C drho1(const T* __restrict__ st, int stride, int c)
@@ -175,18 +217,21 @@ __device__ __forceinline__ void strip_init_barriers(const StripSmem<T, C, NT, NS
 // Walk one strip segment: columns [x0, x0 + min(W, nx - x0)), rows [y0, y1).
 // G counts walk rows over every segment this CTA has walked: row G uses
 // stage G % NS in its (G / NS)-th phase, so segments can follow one another
-// without re-initialising the barriers.  Returns false (with ST_TIMEOUT in
-// bad) if a stage wait gave up; the copies already issued are then drained
-// (bounded) and the CTA must stop.  All threads of the CTA call this with
-// the same arguments.
-template <typename T, typename C, int COLL, int FORC, int NT, int NS>
+// without re-initialising the barriers.  CARRY: a row's pulled populations
+// stay in registers from its psi pass to its collision one iteration later,
+// and its stage is refilled right after the psi pass (NS rows in flight);
+// otherwise the collision re-reads the stage, refilled after it.  Returns
+// false (with ST_TIMEOUT in bad) if a stage wait gave up; the copies already
+// issued are then drained (bounded) and the CTA must stop.  All threads of
+// the CTA call this with the same arguments.
+template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY>
 __device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny,
                                            int x0, int y0, int y1, const Coef<C>& k,
                                            const StripSmem<T, C, NT, NS>& sm, unsigned& G, unsigned& bad)
 {
     using SM = StripSmem<T, C, NT, NS>;
     constexpr int SW = SM::SW, PW = SM::PW;
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31;
     const int wp = min(SM::W, nx - x0);                      // strip width (multiple of 4)
     const int H = y1 - y0;
     const size_t n = (size_t)nx * ny;
@@ -194,9 +239,14 @@ __device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restr
     const unsigned stage_bytes = unsigned(9 * (wp + 8) * sizeof(T));
     const bool left_wrap = x0 == 0, right_wrap = x0 + wp == nx;
     const unsigned base = G;
+    const int c0 = 4 * t;
+    const bool active = c0 < wp;
+    const bool lsm = lane == 0, rsm = (lane == 31) || (c0 + 4 == wp);   // neighbours from shared memory
+    int nissued = 0;
 
-    // Warp 0 issues the nine segment copies of walk row kr into its stage.
-    auto issue = [&](int kr) {
+    // Warp 0 issues the nine segment copies of the next walk row into its stage.
+    auto issue = [&]() {
+        const int kr = nissued++;
         if (t >= 32) return;
         const unsigned g = base + kr;
         uint64_t* bar = &sm.bars[g % NS];
@@ -219,85 +269,80 @@ __device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restr
         }
     };
 
-    for (int kr = 0; kr < NS - 2 && kr < nrows; ++kr) issue(kr);
+    for (int kr = 0; kr < (CARRY ? NS : NS - 2) && kr < nrows; ++kr) issue();
 
-    const int c0 = 4 * t;
-    const bool active = c0 < wp;
-    int kdone = 0;                         // walk rows whose stage wait completed
+    int kdone = 0;
     bool ok_all = true;
-    for (int kk = 0; kk < nrows; ++kk) {
+    C gA[9][4], gB[9][4];
+
+    auto body = [&](int kk, C (&gn)[9][4], C (&gc)[9][4]) -> bool {
         const unsigned g = base + kk;
         const T* st = sm.stages + (g % NS) * 9 * SW;
         const bool ok = mbar_wait(&sm.bars[g % NS], (g / NS) & 1);
-        // psi of walk row kk
         C* prow = sm.psi + (kk & 3) * PW;
         if (ok) {
-            if (active) {
-                C gv[9][4];
-                pull4<T, C>(st, SW, c0, gv);
-                C ps[4];
+            pull4_shfl<T, C>(st, SW, c0, lsm, rsm, gn);
+            C ps[4];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    C s9[9];
+            for (int j = 0; j < 4; ++j) {
+                C s9[9];
 #pragma unroll
-                    for (int a = 0; a < 9; ++a) s9[a] = gv[a][j];
-                    ps[j] = psi_of_rho<C>(k.rho_ref + sum9(s9), k, bad);
-                }
-                sts4(prow + 4 + c0, ps);
+                for (int a = 0; a < 9; ++a) s9[a] = gn[a][j];
+                unsigned b = 0;
+                ps[j] = psi_of_rho<C>(k.rho_ref + sum9(s9), k, b);
+                if (active) bad |= b;
             }
+            if (active) sts4(prow + 4 + c0, ps);
             if (t == 0) prow[3] = psi_of_rho<C>(k.rho_ref + drho1<T, C>(st, SW, -1), k, bad);
             if (t == NT - 1) prow[4 + wp] = psi_of_rho<C>(k.rho_ref + drho1<T, C>(st, SW, wp), k, bad);
         }
-        if (__syncthreads_or(!ok)) {
-            bad |= ST_TIMEOUT;
-            kdone = kk;
-            ok_all = false;
-            break;
-        }
-        kdone = kk + 1;
-        // refill the stage of walk row kk-2 (collided in the previous iteration)
-        if (kk + NS - 2 < nrows) issue(kk + NS - 2);
+        if (__syncthreads_or(!ok)) return false;
+        // Refill a stage every thread is done with: with CARRY the one of row kk
+        // (read only by the psi pass above), otherwise the one of row kk-2 (its
+        // collision ran in the previous iteration, before this barrier).
+        if (nissued < nrows) issue();
         // collide walk row kk-1 (a chunk row when 1 <= kk-1 <= H)
         const int kc = kk - 1;
-        if (kc >= 1 && kc <= H && active) {
-            const T* sc = sm.stages + ((base + kc) % NS) * 9 * SW;
-            C gv[9][4];
-            pull4<T, C>(sc, SW, c0, gv);
-            const C* pm = sm.psi + ((kc - 1) & 3) * PW + 4 + c0;   // row y - 1
-            const C* p0 = sm.psi + (kc & 3) * PW + 4 + c0;         // row y
-            const C* pp = sm.psi + ((kc + 1) & 3) * PW + 4 + c0;   // row y + 1
-            C rm[6], r0[6], rp[6];     // columns c0-1 .. c0+4
-            {
-                C v[4];
-                lds4(pm, v); rm[0] = pm[-1]; rm[1] = v[0]; rm[2] = v[1]; rm[3] = v[2]; rm[4] = v[3]; rm[5] = pm[4];
-                lds4(p0, v); r0[0] = p0[-1]; r0[1] = v[0]; r0[2] = v[1]; r0[3] = v[2]; r0[4] = v[3]; r0[5] = p0[4];
-                lds4(pp, v); rp[0] = pp[-1]; rp[1] = v[0]; rp[2] = v[1]; rp[3] = v[2]; rp[4] = v[3]; rp[5] = pp[4];
+        if (kc >= 1 && kc <= H) {                // uniform over the CTA
+            if (!CARRY) pull4_shfl<T, C>(sm.stages + ((base + kc) % NS) * 9 * SW, SW, c0, lsm, rsm, gc);
+            C rm[6], r0[6], rp[6];               // psi at columns c0-1 .. c0+4 of rows y-1, y, y+1
+            psi_row6<C>(sm.psi + ((kc - 1) & 3) * PW, c0, lsm, rsm, rm);
+            psi_row6<C>(sm.psi + (kc & 3) * PW, c0, lsm, rsm, r0);
+            psi_row6<C>(sm.psi + ((kc + 1) & 3) * PW, c0, lsm, rsm, rp);
+            if (active) {
+                T o[9][4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    Stencil<C> q{r0[j + 1], r0[j + 2], rp[j + 1], r0[j], rm[j + 1],
+                                 rp[j + 2], rp[j], rm[j], rm[j + 2]};
+                    C Fx, Fy, vx, vy, rho, gj[9];
+                    force<C>(q, k, Fx, Fy);
+#pragma unroll
+                    for (int a = 0; a < 9; ++a) gj[a] = gc[a][j];
+                    collide<C, COLL, FORC>(gj, Fx, Fy, k, vx, vy, rho);
+                    if (!isfinite(gj[0])) bad |= ST_NONFINITE;   // g0 closes on all others
+#pragma unroll
+                    for (int a = 0; a < 9; ++a) o[a][j] = T(gj[a]);
+                }
+                const int y = y0 + kc - 1;
+                T* out = fout + (size_t)y * nx + x0 + c0;
+#pragma unroll
+                for (int a = 0; a < 9; ++a) stg4(out + a * n, o[a][0], o[a][1], o[a][2], o[a][3]);
             }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                Stencil<C> q{r0[j + 1], r0[j + 2], rp[j + 1], r0[j], rm[j + 1],
-                             rp[j + 2], rp[j], rm[j], rm[j + 2]};
-                C Fx, Fy, vx, vy, rho, gj[9];
-                force<C>(q, k, Fx, Fy);
-#pragma unroll
-                for (int a = 0; a < 9; ++a) gj[a] = gv[a][j];
-                collide<C, COLL, FORC>(gj, Fx, Fy, k, vx, vy, rho);
-                bad |= finite_bits<C>(gj);
-#pragma unroll
-                for (int a = 0; a < 9; ++a) gv[a][j] = gj[a];
-            }
-            const int y = y0 + kc - 1;
-            T* out = fout + (size_t)y * nx + x0 + c0;
-#pragma unroll
-            for (int a = 0; a < 9; ++a) stg4(out + a * n, T(gv[a][0]), T(gv[a][1]), T(gv[a][2]), T(gv[a][3]));
         }
+        return true;
+    };
+
+    for (int kk = 0; kk < nrows; kk += 2) {
+        if (!body(kk, gA, gB)) { ok_all = false; kdone = kk; break; }
+        if (kk + 1 < nrows && !body(kk + 1, gB, gA)) { ok_all = false; kdone = kk + 1; break; }
+        kdone = kk + 2;
     }
     if (!ok_all) {
+        bad |= ST_TIMEOUT;
         // Drain copies already issued for rows the walk never consumed (bounded).
-        if (t == 0) {
-            const int issued = min(nrows, kdone + NS - 2);
-            for (int kr = kdone; kr < issued; ++kr) mbar_wait(&sm.bars[(base + kr) % NS], ((base + kr) / NS) & 1);
-        }
+        if (t == 0)
+            for (int kr = kdone; kr < nissued; ++kr) mbar_wait(&sm.bars[(base + kr) % NS], ((base + kr) / NS) & 1);
         __syncthreads();
         return false;
     }
@@ -307,7 +352,7 @@ __device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restr
 }
 
 // One lattice, grid (strips, row chunks).
-template <typename T, typename C, int COLL, int FORC, int NT, int NS>
+template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY>
 __global__ void __launch_bounds__(NT)
 k_step_strip(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, int nchunks, Coef<C> k,
              unsigned* __restrict__ status)
@@ -324,7 +369,7 @@ k_step_strip(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, in
     if (y1 <= y0) return;
     strip_init_barriers(sm);
     unsigned G = 0, bad = 0;
-    strip_walk<T, C, COLL, FORC, NT, NS>(fin, fout, nx, ny, x0, y0, y1, k, sm, G, bad);
+    strip_walk<T, C, COLL, FORC, NT, NS, CARRY>(fin, fout, nx, ny, x0, y0, y1, k, sm, G, bad);
     flag_status(bad, status);
 }
 
@@ -337,11 +382,11 @@ constexpr size_t strip_smem()
 // One launch over the whole lattice: strips of 4*NT columns, and as many row
 // chunks as fill every resident CTA slot once (one wave), but no chunk shorter
 // than 16 rows, so the two halo rows per chunk stay a small overhead.
-template <typename T, typename C, int COLL, int FORC, int NT, int NS>
+template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY>
 int launch_strip_cfg(const lbm_params* p, const void* fin, void* fout, unsigned* status, cudaStream_t s)
 {
     constexpr size_t smem = strip_smem<T, C, NT, NS>();
-    auto kern = k_step_strip<T, C, COLL, FORC, NT, NS>;
+    auto kern = k_step_strip<T, C, COLL, FORC, NT, NS, CARRY>;
     static int per_sm = 0, nsm = 0;    // per instantiation (one device per process)
     if (per_sm == 0) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -361,13 +406,13 @@ int launch_strip_cfg(const lbm_params* p, const void* fin, void* fout, unsigned*
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_E_CUDA;
 }
 
-template <typename T, typename C, int NT, int NS>
+template <typename T, typename C, int NT, int NS, bool CARRY = false>
 int launch_strip_scheme(const lbm_params* p, const void* fin, void* fout, unsigned* status, cudaStream_t s)
 {
-    if (p->collision == LBM_MRT) return launch_strip_cfg<T, C, MRT, GUO, NT, NS>(p, fin, fout, status, s);
-    if (p->forcing == LBM_GUO) return launch_strip_cfg<T, C, BGK, GUO, NT, NS>(p, fin, fout, status, s);
-    if (p->forcing == LBM_EDM) return launch_strip_cfg<T, C, BGK, EDM, NT, NS>(p, fin, fout, status, s);
-    return launch_strip_cfg<T, C, BGK, SC, NT, NS>(p, fin, fout, status, s);
+    if (p->collision == LBM_MRT) return launch_strip_cfg<T, C, MRT, GUO, NT, NS, CARRY>(p, fin, fout, status, s);
+    if (p->forcing == LBM_GUO) return launch_strip_cfg<T, C, BGK, GUO, NT, NS, CARRY>(p, fin, fout, status, s);
+    if (p->forcing == LBM_EDM) return launch_strip_cfg<T, C, BGK, EDM, NT, NS, CARRY>(p, fin, fout, status, s);
+    return launch_strip_cfg<T, C, BGK, SC, NT, NS, CARRY>(p, fin, fout, status, s);
 }
 
 }  // namespace lbm
