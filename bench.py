@@ -241,6 +241,8 @@ def run_ours(args):
             tune["%d:t%d/s%d" % (cid, threads, stages)] = e0.elapsed_time(e1) / 10
         lat.init_density(rho0)
         cfg, _ = lat.autotune(10)
+    if args.config >= 0:
+        lat.config = args.config
     chosen = [c for c in lat.configs() if c[0] == lat.config][0]
     variant = lat.variant
     for _ in range(args.warmup):
@@ -322,18 +324,130 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_warmstart(args):
+    """Steps and wall time to steady state, cold vs learned warm start, on
+    held-out instances of the batched sweep, and the plain cold FP64
+    single-lattice path on a subset of them."""
+    import numpy as np
+    import torch
+
+    from paper_1412_5170_gb300 import lbm, synth
+    from paper_1412_5170_gb300 import warmstart as ws
+
+    torch.cuda.set_device(0)
+    A = args.ws_A
+    crit = dict(tol_coex=args.ws_tol, check_every=1000, max_steps=args.ws_max_steps)
+
+    def draw(n, seed):
+        inst = synth.batch_instances(n, seed=seed)
+        for d in inst:
+            d["A"] = A
+        return inst
+
+    t0 = time.perf_counter()
+    train = draw(args.ws_train, 20144000)
+    gen = ws.solve(train, collision="mrt", **crit)
+    ok = gen["state"] == 1
+    net = ws.WarmStart(seed=1)
+    tt = time.perf_counter()
+    losses = net.fit([d for d, k in zip(train, ok) if k], gen["profiles"][ok], epochs=args.ws_epochs)
+    train_s = time.perf_counter() - tt
+
+    test = draw(args.ws_test, 20145000)
+    cold = ws.solve(test, collision="mrt", **crit)
+    pred = net.predict(test)
+    warm = ws.solve(test, collision="mrt", profiles=pred, **crit)
+    both = (cold["state"] == 1) & (warm["state"] == 1)
+    rl_c, rv_c = ws.coexistence(test, cold["obs"])
+    rl_w, rv_w = ws.coexistence(test, warm["obs"])
+    dv = np.abs(rv_w - rv_c) / rv_c
+    dl = np.abs(rl_w - rl_c) / rl_c
+
+    # The plain method for comparison: cold FP64 single-lattice runs to the same
+    # criterion (density change per 1000 steps), one instance at a time.
+    fp64 = []
+    sub = [i for i in np.nonzero(both)[0][:args.ws_fp64]]
+    for i in sub:
+        d = test[i]
+        p = lbm.make_params(d["side"], d["side"], d["T_over_Tc"], d["tau"], A, d["K"], "mrt", "guo", "fp64",
+                            **MRT)
+        with lbm.Lattice(p) as lat:
+            lat.init_preset(d["kind"], d["size"], seed=d["seed"])
+            torch.cuda.synchronize()
+            ts = time.perf_counter()
+            st_code, steps, probes = fp64_run_to_steady(lat, d["kind"], args.ws_tol, 1000, args.ws_max_steps)
+            fp64.append(dict(i=int(i), status=st_code, steps=steps, wall_s=time.perf_counter() - ts,
+                             nodes=d["side"] ** 2, rho_l=probes[0], rho_v=probes[1],
+                             rel_to_fp32_cold=[abs(probes[0] - rl_c[i]) / rl_c[i], abs(probes[1] - rv_c[i]) / rv_c[i]]))
+    fp64_nodesteps_per_s = (sum(r["steps"] * r["nodes"] for r in fp64) / max(sum(r["wall_s"] for r in fp64), 1e-9)
+                            if fp64 else None)
+    cold_rate = sum(cold["steps"][i] * test[i]["side"] ** 2 for i in range(len(test))) / cold["wall_s"]
+    line = {
+        "metric": "steps-to-steady warm vs cold", "unit": "steps",
+        "value": float(np.median(warm["steps"][both])) if both.any() else None,
+        "cold_median_steps": float(np.median(cold["steps"][both])) if both.any() else None,
+        "warm_over_cold_steps_mean": float(np.mean(warm["steps"][both] / cold["steps"][both])) if both.any() else None,
+        "wall_s": {"cold_batch": cold["wall_s"], "warm_batch": warm["wall_s"], "train_data": gen["wall_s"],
+                   "training": train_s, "total": time.perf_counter() - t0},
+        "instances": {"train": len(train), "train_converged": int(ok.sum()), "test": len(test),
+                      "cold_converged": int((cold["state"] == 1).sum()),
+                      "warm_converged": int((warm["state"] == 1).sum()),
+                      "failed_cold": int((cold["state"] == 2).sum()), "both": int(both.sum())},
+        "coexistence_warm_vs_cold": {"vapour_rel_median": float(np.median(dv[both])) if both.any() else None,
+                                     "vapour_rel_max": float(np.max(dv[both])) if both.any() else None,
+                                     "liquid_rel_max": float(np.max(dl[both])) if both.any() else None},
+        "fp64_plain": {"instances": fp64, "node_steps_per_s": fp64_nodesteps_per_s},
+        "batched_fp32_node_steps_per_s_cold": cold_rate,
+        "criterion": {"coexistence_rel_change_per_1000_steps": args.ws_tol, "max_steps": args.ws_max_steps},
+        "train_loss": losses,
+        "config": {"workload": "batched sweep: side in {64..512}, T/Tc U[.5,.9], tau U[.55,1.2], K U[1/16,1], "
+                               "R U[10, side/4], droplet or slab; MRT+Guo, A=%g, FP32 deviations" % A},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def fp64_run_to_steady(lat, kind, tol, every, max_steps):
+    """Cold single-lattice run until both coexistence densities (centre and
+    corner, or mid and edge row for a slab) change by less than tol relative
+    per `every` steps -- the batched runs' criterion -- on the FP64 path."""
+    def probes(st):
+        return (st["rho_row_mid"], st["rho_row0"]) if kind == "slab" else (st["rho_center"], st["rho_corner"])
+    prev = probes(lat.stats())
+    steps = 0
+    while steps < max_steps:
+        lat.step(every)
+        steps += every
+        st = lat.stats()
+        if st["status"] != 0:
+            return st["status"], steps, prev
+        cur = probes(st)
+        if max(abs(cur[0] - prev[0]) / cur[0], abs(cur[1] - prev[1]) / cur[1]) < tol:
+            return 0, steps, cur
+        prev = cur
+    return 6, steps, prev
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="throughput", choices=["throughput", "warmstart"])
+    ap.add_argument("--ws-train", type=int, default=2000)
+    ap.add_argument("--ws-test", type=int, default=256)
+    ap.add_argument("--ws-epochs", type=int, default=1500)
+    ap.add_argument("--ws-fp64", type=int, default=4, help="held-out instances also run on the FP64 path")
+    ap.add_argument("--ws-A", type=float, default=-0.5)
+    ap.add_argument("--ws-tol", type=float, default=1e-5, help="coexistence-density change per 1000 steps")
+    ap.add_argument("--ws-max-steps", type=int, default=100000)
     ap.add_argument("--cpu-steps", type=int, default=300,
                     help="oracle steps on one 256x256 cell for cpu_baseline (0 = skip)")
     ap.add_argument("--size", type=int, default=4096, help="lattice side (multiple of 256; profiling)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false", help="skip the end-to-end leg")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default kernel configuration")
+    ap.add_argument("--config", type=int, default=-1, help="force a kernel configuration id (profiling)")
     args = ap.parse_args()
     global N_SIDE
     if args.size % CELL:
@@ -343,6 +457,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "warmstart":
+        run_warmstart(args)
     else:
         run_ours(args)
 

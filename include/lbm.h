@@ -256,13 +256,16 @@ int lbm_batch_init(lbm_batch *b, const double *profiles_dev, const int32_t *use_
 int lbm_batch_step(lbm_batch *b, int64_t nsteps);
 
 /* Step every running instance, checking each every check_every steps: an
- * instance converges when max|v(t) - v(t - check_every)| < tol_v or
- * max|rho(t) - rho(t - check_every)|/rho < tol_rho (a tolerance <= 0 is
- * ignored) and fails when a kernel flags a non-finite or out-of-domain value;
- * either way it stops stepping while the others go on.  Returns LBM_OK when no
+ * instance converges when max|v(t) - v(t - check_every)| < tol_v, when
+ * max|rho(t) - rho(t - check_every)|/rho < tol_rho, or when both of its
+ * coexistence densities (liquid and vapour probe: centre and corner node of
+ * a droplet or bubble, mid and edge row of a slab) changed by less than
+ * tol_coex relative since the previous check (a tolerance <= 0 is ignored);
+ * it fails when a kernel flags a non-finite or out-of-domain value.  Either
+ * way it stops stepping while the others go on.  Returns LBM_OK when no
  * instance is left running, LBM_E_NOT_CONVERGED at max_steps. */
-int lbm_batch_run_to_steady(lbm_batch *b, double tol_v, double tol_rho, int64_t check_every, int64_t max_steps,
-                            int64_t *steps_done);
+int lbm_batch_run_to_steady(lbm_batch *b, double tol_v, double tol_rho, double tol_coex, int64_t check_every,
+                            int64_t max_steps, int64_t *steps_done);
 
 /* Recompute the observables of every instance (no decisions, no snapshot change). */
 int lbm_batch_observe(lbm_batch *b);

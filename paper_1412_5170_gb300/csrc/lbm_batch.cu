@@ -49,7 +49,9 @@ struct BPart {
     unsigned status, pad;
 };
 enum : int { B_RUNNING = 0, B_CONVERGED = 1, B_FAILED = 2 };
-struct __align__(32) Snap { double vx, vy, rho, pad; };   // convergence snapshot per node
+// Convergence snapshot per node in the compute type: v and the density
+// deviation drho (rho = rho_ref + drho).
+struct __align__(16) Snap { float vx, vy, drho, pad; };
 
 constexpr int kBatchWarps = 1;   // warps (independent 128-column walkers) per CTA
 
@@ -136,7 +138,11 @@ k_observe_batch(const float* __restrict__ f, const BInst* __restrict__ inst, con
     __syncthreads();
     const int tx = threadIdx.x % GTX, ty = threadIdx.x / GTX;
     const int x = x0 + tx, y = y0 + ty;
-    double v[8] = {0, 0, 0, -1e300, -1e300, -1e300, -1e300, -1e300};
+    // Per-node work in FP32 (maxima are exact in any precision; only the
+    // mass and probe-row sums take FP64 arithmetic, the row sums only in the
+    // warps that hold those rows: a warp is one tile row).
+    double rho = 0;
+    float mv = 0.f, dv = 0.f, dr = 0.f, dmax = -1e30f, ndmin = -1e30f;
     if (x < nx && y < ny) {
         float g[9];
         pull_node<float, float>(fi, x, y, nx, ny, n, g);
@@ -147,32 +153,40 @@ k_observe_batch(const float* __restrict__ f, const BInst* __restrict__ inst, con
         force<float>(q, k, Fx, Fy);
         moments<float>(g, drho, jx, jy);
         const float rc = k.rho_ref + drho;
-        const double rho = double(k.rho_ref) + double(drho);
-        const double vx = double(jx / rc + 0.5f * Fx / rc);
-        const double vy = double(jy / rc + 0.5f * Fy / rc);
-        if (!isfinite(rho) || !isfinite(vx) || !isfinite(vy)) bad |= ST_NONFINITE;
+        rho = double(k.rho_ref) + double(drho);
+        const float vx = jx / rc + 0.5f * Fx / rc;
+        const float vy = jy / rc + 0.5f * Fy / rc;
+        if (!isfinite(drho) || !isfinite(vx) || !isfinite(vy)) bad |= ST_NONFINITE;
         const size_t o = (size_t)I->node_off + (size_t)y * nx + x;
         if (mode & BO_RHO) rho_out[o] = rho;
-        double dv = 1e300, dr = 1e300;
+        dv = 1e30f;
+        dr = 1e30f;
         if (mode & BO_SNAP) {
             const Snap s = snap[o];
-            dv = hypot(vx - s.vx, vy - s.vy);
-            dr = fabs(rho - s.rho) / rho;
-            if (isnan(dv)) dv = 1e300;
-            if (isnan(dr)) dr = 1e300;
-            snap[o] = Snap{vx, vy, rho, 0.0};
+            const float ddx = vx - s.vx, ddy = vy - s.vy;
+            dv = sqrtf(ddx * ddx + ddy * ddy);
+            dr = fabsf(drho - s.drho) / rc;
+            if (isnan(dv)) dv = 1e30f;
+            if (isnan(dr)) dr = 1e30f;
+            snap[o] = Snap{vx, vy, drho, 0.f};
         }
-        double mv = hypot(vx, vy);
-        if (isnan(mv)) mv = 1e300;
-        v[0] = rho;
-        v[1] = (y == ny / 2) ? rho : 0.0;
-        v[2] = (y == 0) ? rho : 0.0;
-        v[3] = mv; v[4] = dv; v[5] = dr; v[6] = rho; v[7] = -rho;
+        mv = sqrtf(vx * vx + vy * vy);
+        if (isnan(mv)) mv = 1e30f;
+        dmax = drho;
+        ndmin = -drho;
         if (x == nx / 2 && y == ny / 2) obs[tl.inst].rho_center = rho;
         if (x == 0 && y == 0) obs[tl.inst].rho_corner = rho;
     }
-    for (int j = 0; j < 3; ++j) v[j] = warp_sum(v[j]);
-    for (int j = 3; j < 8; ++j) v[j] = warp_max(v[j]);
+    const bool mid_row = y == ny / 2, row_0 = y == 0;   // uniform over the warp
+    double v[8];
+    v[0] = warp_sum(rho);
+    v[1] = mid_row ? warp_sum(rho) : 0.0;
+    v[2] = row_0 ? warp_sum(rho) : 0.0;
+    v[3] = double(warp_max(mv));
+    v[4] = double(warp_max(dv));
+    v[5] = double(warp_max(dr));
+    v[6] = double(k.rho_ref) + double(warp_max(dmax));
+    v[7] = -(double(k.rho_ref) + double(-warp_max(ndmin)));
     const unsigned wb = __reduce_or_sync(0xffffffffu, bad);
     const int wid = threadIdx.x / 32;
     __syncthreads();
@@ -197,12 +211,15 @@ k_observe_batch(const float* __restrict__ f, const BInst* __restrict__ inst, con
 
 // Per-instance fixed-order reduction of the tile partials, then the
 // convergence / failure decision: a running instance stops as converged when
-// max|v - v_snap| < tol_v or max|rho - rho_snap|/rho < tol_rho (either
-// tolerance <= 0 disables it), and as failed when a kernel flagged it.
+// max|v - v_snap| < tol_v, max|rho - rho_snap|/rho < tol_rho, or both of its
+// coexistence densities (liquid and vapour probe: centre and corner node of a
+// droplet or bubble, mid and edge row of a slab) changed by less than tol_coex
+// relative since the previous check (a tolerance <= 0 disables it), and as
+// failed when a kernel flagged it.
 __global__ void __launch_bounds__(256)
 k_reduce_batch(const BInst* __restrict__ inst, const BPart* __restrict__ parts, int* __restrict__ state,
                int* __restrict__ fail_code, const unsigned* __restrict__ inst_status, BObs* __restrict__ obs,
-               double tol_v, double tol_rho, int decide, int all)
+               double2* __restrict__ probe_prev, double tol_v, double tol_rho, double tol_coex, int decide, int all)
 {
     const int i = blockIdx.x;
     if (!all && state[i] != B_RUNNING) return;
@@ -242,12 +259,18 @@ k_reduce_batch(const BInst* __restrict__ inst, const BPart* __restrict__ parts, 
         o.rho_min = -red[7][0];
         const unsigned b = sbad[0] | inst_status[i];
         if (!decide || state[i] != B_RUNNING) return;
+        const bool slab = I->kind == LBM_SLAB;
+        const double pl = slab ? o.rho_row_mid : o.rho_center, pv = slab ? o.rho_row0 : o.rho_corner;
+        const double2 pp = probe_prev[i];
+        const double dcoex = fmax(fabs(pl - pp.x) / fabs(pl), fabs(pv - pp.y) / fabs(pv));   // NaN before the first check
+        probe_prev[i] = make_double2(pl, pv);
         if (b) {
             state[i] = B_FAILED;
             fail_code[i] = (b & ST_NONFINITE) ? LBM_E_NONFINITE
                            : (b & ST_EOS) ? LBM_E_EOS_DOMAIN
                            : (b & ST_TIMEOUT) ? LBM_E_TIMEOUT : LBM_E_CUDA;
-        } else if ((tol_v > 0 && o.max_dv < tol_v) || (tol_rho > 0 && o.max_drho < tol_rho)) {
+        } else if ((tol_v > 0 && o.max_dv < tol_v) || (tol_rho > 0 && o.max_drho < tol_rho) ||
+                   (tol_coex > 0 && dcoex < tol_coex)) {
             state[i] = B_CONVERGED;
         }
     }
@@ -400,6 +423,7 @@ struct lbm_batch {
     int* fail = nullptr;         // device
     unsigned* status = nullptr;  // device, per instance
     BObs* obs = nullptr;         // device
+    double2* probe_prev = nullptr;   // device: coexistence probes at the previous check
     // pinned host mirrors
     int* h_state = nullptr;
     int* h_fail = nullptr;
@@ -413,7 +437,7 @@ struct lbm_batch {
     // graph cache
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     long long g_every = 0;
-    double g_tol_v = 0, g_tol_rho = 0;
+    double g_tol_v = 0, g_tol_rho = 0, g_tol_coex = 0;
 };
 
 namespace {
@@ -510,15 +534,16 @@ int step_once(lbm_batch* b)
 }
 
 // mode: BO_* flags; decide: apply the convergence / failure decision.
-int observe(lbm_batch* b, int mode, double tol_v, double tol_rho, int decide)
+int observe(lbm_batch* b, int mode, double tol_v, double tol_rho, double tol_coex, int decide)
 {
     if (b->ntiles) {
         k_observe_batch<<<b->ntiles, GTX * GTY, 0, b->stream>>>(b->f[b->cur], b->dinst, b->tiles, b->state, b->snap,
                                                                b->rho, b->parts, b->obs, mode);
         B_CUDA(cudaGetLastError());
     }
-    k_reduce_batch<<<b->n, 256, 0, b->stream>>>(b->dinst, b->parts, b->state, b->fail, b->status, b->obs, tol_v,
-                                                 tol_rho, decide, (mode & BO_ALL) ? 1 : 0);
+    k_reduce_batch<<<b->n, 256, 0, b->stream>>>(b->dinst, b->parts, b->state, b->fail, b->status, b->obs,
+                                                 b->probe_prev, tol_v, tol_rho, tol_coex, decide,
+                                                 (mode & BO_ALL) ? 1 : 0);
     B_CUDA(cudaGetLastError());
     B_CUDA(cudaMemcpyAsync(b->h_state, b->state, sizeof(int) * b->n, cudaMemcpyDeviceToHost, b->stream));
     B_CUDA(cudaMemcpyAsync(b->h_fail, b->fail, sizeof(int) * b->n, cudaMemcpyDeviceToHost, b->stream));
@@ -528,13 +553,14 @@ int observe(lbm_batch* b, int mode, double tol_v, double tol_rho, int decide)
 
 // One check interval: `every` steps, then observe + decide.  Captured once in
 // a CUDA graph per buffer parity and replayed.
-int interval(lbm_batch* b, long long every, double tol_v, double tol_rho)
+int interval(lbm_batch* b, long long every, double tol_v, double tol_rho, double tol_coex)
 {
-    if (b->g_every != every || b->g_tol_v != tol_v || b->g_tol_rho != tol_rho) {
+    if (b->g_every != every || b->g_tol_v != tol_v || b->g_tol_rho != tol_rho || b->g_tol_coex != tol_coex) {
         drop_graphs(b);
         b->g_every = every;
         b->g_tol_v = tol_v;
         b->g_tol_rho = tol_rho;
+        b->g_tol_coex = tol_coex;
     }
     const int parity = b->cur;
     if (!b->gexec[parity]) {
@@ -542,7 +568,7 @@ int interval(lbm_batch* b, long long every, double tol_v, double tol_rho)
         B_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
         int s = LBM_OK;
         for (long long i = 0; i < every && s == LBM_OK; ++i) s = step_once(b);
-        if (s == LBM_OK) s = observe(b, BO_SNAP, tol_v, tol_rho, 1);
+        if (s == LBM_OK) s = observe(b, BO_SNAP, tol_v, tol_rho, tol_coex, 1);
         const cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
         b->cur = parity;   // capture recorded the launches; the state did not move
         if (s != LBM_OK) return s;
@@ -645,6 +671,7 @@ int lbm_batch_create(const lbm_batch_params* bp, const lbm_instance* inst, int n
     if ((e = cudaMalloc(&b->fail, sizeof(int) * n)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&b->status, sizeof(unsigned) * n)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&b->obs, sizeof(BObs) * n)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&b->probe_prev, sizeof(double2) * n)) != cudaSuccess) return fail(e);
     if ((e = cudaMallocHost(&b->h_state, sizeof(int) * n)) != cudaSuccess) return fail(e);
     if ((e = cudaMallocHost(&b->h_fail, sizeof(int) * n)) != cudaSuccess) return fail(e);
     if ((e = cudaMallocHost(&b->h_obs, sizeof(BObs) * n)) != cudaSuccess) return fail(e);
@@ -683,6 +710,7 @@ void lbm_batch_destroy(lbm_batch* b)
     cudaFree(b->fail);
     cudaFree(b->status);
     cudaFree(b->obs);
+    cudaFree(b->probe_prev);
     cudaFreeHost(b->h_state);
     cudaFreeHost(b->h_fail);
     cudaFreeHost(b->h_obs);
@@ -696,6 +724,7 @@ static int reset_run_state(lbm_batch* b)
     B_CUDA(cudaMemsetAsync(b->fail, 0, sizeof(int) * b->n, b->stream));
     B_CUDA(cudaMemsetAsync(b->status, 0, sizeof(unsigned) * b->n, b->stream));
     B_CUDA(cudaMemsetAsync(b->obs, 0, sizeof(BObs) * b->n, b->stream));
+    B_CUDA(cudaMemsetAsync(b->probe_prev, 0xff, sizeof(double2) * b->n, b->stream));   // NaN: no previous check
     long long nodes = 0;
     for (const BInst& I : b->hinst) nodes = std::max<long long>(nodes, I.node_off + (long long)I.nx * I.ny);
     B_CUDA(cudaMemsetAsync(b->snap, 0xff, sizeof(Snap) * nodes, b->stream));   // NaN: no snapshot yet
@@ -742,16 +771,17 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps)
 int lbm_batch_observe(lbm_batch* b)
 {
     if (!b) return LBM_E_INVALID;
-    const int s = observe(b, BO_RHO | BO_ALL, 0, 0, 0);
+    const int s = observe(b, BO_RHO | BO_ALL, 0, 0, 0, 0);
     if (s != LBM_OK) return s;
     B_CUDA(cudaStreamSynchronize(b->stream));
     return LBM_OK;
 }
 
-int lbm_batch_run_to_steady(lbm_batch* b, double tol_v, double tol_rho, int64_t check_every, int64_t max_steps,
-                            int64_t* steps_done)
+int lbm_batch_run_to_steady(lbm_batch* b, double tol_v, double tol_rho, double tol_coex, int64_t check_every,
+                            int64_t max_steps, int64_t* steps_done)
 {
-    if (!b || check_every < 1 || max_steps < 0 || (!(tol_v > 0) && !(tol_rho > 0))) return LBM_E_INVALID;
+    if (!b || check_every < 1 || max_steps < 0 || (!(tol_v > 0) && !(tol_rho > 0) && !(tol_coex > 0)))
+        return LBM_E_INVALID;
     int64_t done = 0;
     int active = 0;
     for (int i = 0; i < b->n; ++i) active += b->h_state[i] == B_RUNNING;
@@ -762,11 +792,11 @@ int lbm_batch_run_to_steady(lbm_batch* b, double tol_v, double tol_rho, int64_t 
         std::copy(b->h_state, b->h_state + b->n, before.begin());   // the graph's copy-out rewrites h_state
         int s;
         if (k == check_every) {
-            s = interval(b, k, tol_v, tol_rho);
+            s = interval(b, k, tol_v, tol_rho, tol_coex);
         } else {   // last partial interval: plain launches
             s = LBM_OK;
             for (int64_t i = 0; i < k && s == LBM_OK; ++i) s = step_once(b);
-            if (s == LBM_OK) s = observe(b, BO_SNAP, tol_v, tol_rho, 1);
+            if (s == LBM_OK) s = observe(b, BO_SNAP, tol_v, tol_rho, tol_coex, 1);
         }
         if (s != LBM_OK) return s;
         B_CUDA(cudaStreamSynchronize(b->stream));             // h_state now holds the decision of this interval
@@ -801,7 +831,7 @@ int lbm_batch_results(lbm_batch* b, int32_t* state, int32_t* code, int64_t* step
 int lbm_batch_read_density(lbm_batch* b, int i, double* rho_host)
 {
     if (!b || i < 0 || i >= b->n || !rho_host) return LBM_E_INVALID;
-    const int s = observe(b, BO_RHO | BO_ALL, 0, 0, 0);
+    const int s = observe(b, BO_RHO | BO_ALL, 0, 0, 0, 0);
     if (s != LBM_OK) return s;
     const BInst& I = b->hinst[i];
     B_CUDA(cudaMemcpyAsync(rho_host, b->rho + I.node_off, sizeof(double) * I.nx * I.ny, cudaMemcpyDeviceToHost,
@@ -815,7 +845,7 @@ int lbm_batch_profiles(lbm_batch* b, int nb, double smax, double* prof_host)
     if (!b || nb < 2 || nb > 1024 || !(smax > 0) || !prof_host) return LBM_E_INVALID;
     double* dprof = nullptr;
     B_CUDA(cudaMalloc(&dprof, sizeof(double) * nb * b->n));
-    int s = observe(b, BO_RHO | BO_ALL, 0, 0, 0);
+    int s = observe(b, BO_RHO | BO_ALL, 0, 0, 0, 0);
     if (s == LBM_OK) {
         k_radial_profile<<<dim3(nb, b->n), 128, 0, b->stream>>>(b->dinst, b->rho, nb, smax, dprof);
         s = cuda_ok(cudaGetLastError());

@@ -123,7 +123,23 @@ __device__ __forceinline__ double warp_max(double v)
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
+__device__ __forceinline__ float warp_max(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+template <typename C> __device__ __forceinline__ C obs_huge();
+template <> __device__ __forceinline__ double obs_huge<double>() { return 1e300; }
+template <> __device__ __forceinline__ float obs_huge<float>() { return 1e30f; }
 
+// The per-node work stays in the compute type C: |v|, |v - v_snap| and the
+// density extremes (tracked as max drho and max -drho, then rho = rho_ref +
+// drho once per block -- exact, since that sum rounds monotonically in drho)
+// are maxima, which are exact in any precision, so only the mass and the two
+// probe-row sums need FP64 arithmetic; the row sums are taken only by the
+// warps that hold those rows (a warp is one tile row).  This keeps the FP32
+// path off the FP64 pipe, which is narrow on this GPU.
 template <typename T, typename C>
 __global__ void __launch_bounds__(GTX * GTY)
 k_observe(const T* __restrict__ fin, int nx, int ny, Coef<C> k, int mode,
@@ -146,7 +162,8 @@ k_observe(const T* __restrict__ fin, int nx, int ny, Coef<C> k, int mode,
     __syncthreads();
     const int tx = threadIdx.x % GTX, ty = threadIdx.x / GTX;
     const int x = x0 + tx, y = y0 + ty;
-    double mass = 0, row_mid = 0, row0 = 0, mv = 0, mdv = 0, rmax = -1e300, nrmin = -1e300;
+    double mass = 0, rho = 0;
+    C mv = 0, mdv = 0, dmax = -obs_huge<C>(), ndmin = -obs_huge<C>();
     if (x < nx && y < ny) {
         C g[9];
         pull_node<T, C>(fin, x, y, nx, ny, n, g);
@@ -156,37 +173,40 @@ k_observe(const T* __restrict__ fin, int nx, int ny, Coef<C> k, int mode,
         C Fx, Fy, drho, jx, jy;
         force<C>(q, k, Fx, Fy);
         moments<C>(g, drho, jx, jy);
-        const double rho = double(k.rho_ref) + double(drho);
+        rho = double(k.rho_ref) + double(drho);
         const C rc = k.rho_ref + drho;
-        const double vx = double(jx / rc + C(0.5) * Fx / rc);
-        const double vy = double(jy / rc + C(0.5) * Fy / rc);
-        if (!isfinite(rho) || !isfinite(vx) || !isfinite(vy)) bad |= ST_NONFINITE;
+        const C vx = jx / rc + C(0.5) * Fx / rc;
+        const C vy = jy / rc + C(0.5) * Fy / rc;
+        if (!isfinite(drho) || !isfinite(vx) || !isfinite(vy)) bad |= ST_NONFINITE;
         const size_t o = (size_t)y * nx + x;
         if (mode & OBS_FIELDS) {
             if (rho_o) rho_o[o] = rho;
-            if (vx_o) vx_o[o] = vx;
-            if (vy_o) vy_o[o] = vy;
+            if (vx_o) vx_o[o] = double(vx);
+            if (vy_o) vy_o[o] = double(vy);
         }
         if (mode & OBS_SNAP_CMP) {
             const double2 s = vsnap[o];
-            mdv = hypot(vx - s.x, vy - s.y);
-            if (isnan(mdv)) mdv = 1e300;
+            const C dx = vx - C(s.x), dy = vy - C(s.y);
+            mdv = sqrt(dx * dx + dy * dy);
+            if (isnan(mdv)) mdv = obs_huge<C>();
         }
-        if (mode & OBS_SNAP_STORE) vsnap[o] = make_double2(vx, vy);
+        if (mode & OBS_SNAP_STORE) vsnap[o] = make_double2(double(vx), double(vy));
         mass = rho;
-        if (y == ny / 2) row_mid = rho;
-        if (y == 0) row0 = rho;
-        mv = hypot(vx, vy);
-        if (isnan(mv)) mv = 1e300;
-        rmax = rho;
-        nrmin = -rho;
+        mv = sqrt(vx * vx + vy * vy);
+        if (isnan(mv)) mv = obs_huge<C>();
+        dmax = drho;
+        ndmin = -drho;
         if (ds && x == nx / 2 && y == ny / 2) ds->rho_center = rho;
         if (ds && x == 0 && y == 0) ds->rho_corner = rho;
     }
     if (mode & OBS_REDUCE) {
         const unsigned allbad = __reduce_or_sync(0xffffffffu, bad);
-        double v[7] = {warp_sum(mass), warp_sum(row_mid), warp_sum(row0), warp_max(mv),
-                       warp_max(mdv), warp_max(rmax), warp_max(nrmin)};
+        const bool mid_row = y == ny / 2, row_0 = y == 0;      // uniform over the warp
+        double v[7] = {warp_sum(mass), mid_row ? warp_sum(rho) : 0.0, row_0 ? warp_sum(rho) : 0.0,
+                       double(warp_max(mv)), double(warp_max(mdv)), 0.0, 0.0};
+        const C wdmax = warp_max(dmax), wndmin = warp_max(ndmin);
+        v[5] = double(k.rho_ref) + double(wdmax);
+        v[6] = -(double(k.rho_ref) + double(-wndmin));
         __shared__ unsigned sbad;
         if (threadIdx.x == 0) sbad = 0;
         __syncthreads();

@@ -3,7 +3,9 @@
 // collision with Guo/EDM/SC forcing) for lattices with nx % 4 == 0.
 //
 // Each CTA owns a strip of W = 4*NT columns and a chunk of rows, and walks
-// down its rows.  For density row r it needs the pulled populations
+// its rows one by one: up on even chunks, down on odd ones, so the halo rows
+// that two neighbouring chunks share are read by both at about the same time
+// (the start or the end of both walks) and the second read hits L2.  For density row r it needs the pulled populations
 // f*_a(x - e_a) on row r and one column of halo on each side; those come
 // from nine row segments (one per direction, source row r - e_y(a), columns
 // x0-4 .. x0+W+4) that one warp copies into a shared-memory ring of NS
@@ -19,7 +21,7 @@
 //   4. refill the stage freed by row k-2 with row k-2+NS (one warp)
 //   5. collide row k-1: pulled populations from its stage, F from psi rows
 //      k-2..k, nine 128-bit stores of the post-collision deviations
-// Rows 0 and H+1 of the walk are the halo rows above and below the chunk.
+// Rows 0 and H+1 of the walk are the halo rows before and after the chunk.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -222,11 +224,14 @@ __device__ __forceinline__ void strip_init_barriers(const StripSmem<T, C, NT, NS
 // and its stage is refilled right after the psi pass (NS rows in flight);
 // otherwise the collision re-reads the stage, refilled after it.  Returns
 // false (with ST_TIMEOUT in bad) if a stage wait gave up; the copies already
-// issued are then drained (bounded) and the CTA must stop.  All threads of
-// the CTA call this with the same arguments.
+// issued are then drained (bounded) and the CTA must stop.  down: walk the
+// rows from y1 - 1 to y0 instead of y0 to y1 - 1 (walk row kr is density row
+// y1 - kr instead of y0 - 1 + kr; the psi rows y - 1 and y + 1 of the
+// stencil swap ring slots).  All threads of the CTA call this with the same
+// arguments.
 template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY>
 __device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny,
-                                           int x0, int y0, int y1, const Coef<C>& k,
+                                           int x0, int y0, int y1, bool down, const Coef<C>& k,
                                            const StripSmem<T, C, NT, NS>& sm, unsigned& G, unsigned& bad)
 {
     using SM = StripSmem<T, C, NT, NS>;
@@ -256,7 +261,7 @@ __device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restr
         if (t < 9) {
             fence_proxy_async();   // order earlier generic reads of this slot before the async writes
             const int a = t;
-            const int r = wrap_any(y0 - 1 + kr - ey(a), ny);
+            const int r = wrap_any((down ? y1 - kr : y0 - 1 + kr) - ey(a), ny);
             const T* row = fin + a * n + (size_t)r * nx;
             T* dst = st + a * SW;
             if (!left_wrap && !right_wrap) {
@@ -306,9 +311,9 @@ __device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restr
         if (kc >= 1 && kc <= H) {                // uniform over the CTA
             if (!CARRY) pull4_shfl<T, C>(sm.stages + ((base + kc) % NS) * 9 * SW, SW, c0, lsm, rsm, gc);
             C rm[6], r0[6], rp[6];               // psi at columns c0-1 .. c0+4 of rows y-1, y, y+1
-            psi_row6<C>(sm.psi + ((kc - 1) & 3) * PW, c0, lsm, rsm, rm);
+            psi_row6<C>(sm.psi + ((down ? kc + 1 : kc - 1) & 3) * PW, c0, lsm, rsm, rm);
             psi_row6<C>(sm.psi + (kc & 3) * PW, c0, lsm, rsm, r0);
-            psi_row6<C>(sm.psi + ((kc + 1) & 3) * PW, c0, lsm, rsm, rp);
+            psi_row6<C>(sm.psi + ((down ? kc - 1 : kc + 1) & 3) * PW, c0, lsm, rsm, rp);
             if (active) {
                 T o[9][4];
 #pragma unroll
@@ -324,7 +329,7 @@ __device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restr
 #pragma unroll
                     for (int a = 0; a < 9; ++a) o[a][j] = T(gj[a]);
                 }
-                const int y = y0 + kc - 1;
+                const int y = down ? y1 - kc : y0 + kc - 1;
                 T* out = fout + (size_t)y * nx + x0 + c0;
 #pragma unroll
                 for (int a = 0; a < 9; ++a) stg4(out + a * n, o[a][0], o[a][1], o[a][2], o[a][3]);
@@ -369,7 +374,8 @@ k_step_strip(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, in
     if (y1 <= y0) return;
     strip_init_barriers(sm);
     unsigned G = 0, bad = 0;
-    strip_walk<T, C, COLL, FORC, NT, NS, CARRY>(fin, fout, nx, ny, x0, y0, y1, k, sm, G, bad);
+    strip_walk<T, C, COLL, FORC, NT, NS, CARRY>(fin, fout, nx, ny, x0, y0, y1, (blockIdx.y & 1) != 0, k, sm, G,
+                                                bad);
     flag_status(bad, status);
 }
 

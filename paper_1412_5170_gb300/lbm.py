@@ -108,7 +108,7 @@ _PROTOS = {
     "lbm_batch_destroy": (None, [_vp]),
     "lbm_batch_init": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double]),
     "lbm_batch_step": (ctypes.c_int, [_vp, _i64]),
-    "lbm_batch_run_to_steady": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _i64, _i64,
+    "lbm_batch_run_to_steady": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, _i64, _i64,
                                                ctypes.POINTER(_i64)]),
     "lbm_batch_observe": (ctypes.c_int, [_vp]),
     "lbm_batch_results": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
@@ -367,10 +367,10 @@ class Batch:
     def step(self, n: int):
         check(lbm_batch_step(self.h, int(n)), "lbm_batch_step")
 
-    def run_to_steady(self, tol_v=0.0, tol_rho=0.0, check_every=1000, max_steps=10 ** 6):
+    def run_to_steady(self, tol_v=0.0, tol_rho=0.0, tol_coex=0.0, check_every=1000, max_steps=10 ** 6):
         done = _i64()
-        st = lbm_batch_run_to_steady(self.h, float(tol_v), float(tol_rho), int(check_every), int(max_steps),
-                                     ctypes.byref(done))
+        st = lbm_batch_run_to_steady(self.h, float(tol_v), float(tol_rho), float(tol_coex), int(check_every),
+                                     int(max_steps), ctypes.byref(done))
         return st, done.value
 
     def observe(self):

@@ -29,7 +29,7 @@ def features(inst) -> list:
     return [inst["T_over_Tc"], inst["tau"], inst["A"], inst["K"], inst["size"]]
 
 
-def solve(instances, collision="bgk", tol_v=0.0, tol_rho=1e-6, check_every=1000, max_steps=200000,
+def solve(instances, collision="mrt", tol_v=0.0, tol_rho=0.0, tol_coex=1e-5, check_every=1000, max_steps=100000,
           profiles=None, tune=True):
     """Run a batch to steady state.  profiles: optional (n, NB) densities for
     a warm start (rows of NaN start from the preset).  Returns a dict with
@@ -47,7 +47,8 @@ def solve(instances, collision="bgk", tol_v=0.0, tol_rho=1e-6, check_every=1000,
             b.init(dev, use, SMAX)
         if tune:
             b.autotune(3)
-        st, done = b.run_to_steady(tol_v=tol_v, tol_rho=tol_rho, check_every=check_every, max_steps=max_steps)
+        st, done = b.run_to_steady(tol_v=tol_v, tol_rho=tol_rho, tol_coex=tol_coex, check_every=check_every,
+                                   max_steps=max_steps)
         wall = time.perf_counter() - t0
         state, code, steps, obs = b.results()
         prof = b.profiles(NB, SMAX)

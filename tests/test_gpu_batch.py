@@ -85,6 +85,27 @@ def test_run_to_steady_isolates_failures_and_converges_the_rest(lbm):
     assert done == max(steps)
 
 
+def test_coexistence_criterion_stops_when_probes_settle(lbm):
+    """tol_coex: both coexistence probes (centre/corner, or mid/edge row) stop
+    changing; the final probes match a much longer run."""
+    inst = [dict(side=64, kind="droplet", T_over_Tc=0.85, tau=1.0, A=-0.5, K=1.0, size=16.0, seed=11),
+            dict(nx=16, ny=96, kind="slab", T_over_Tc=0.8, tau=0.8, A=-0.5, K=0.5, size=24.0, seed=12)]
+    with lbm.Batch(inst, collision="mrt") as b:
+        b.init()
+        st, done = b.run_to_steady(tol_coex=1e-5, check_every=1000, max_steps=100000)
+        state, _, steps, obs = b.results()
+    assert st == lbm.OK and list(state) == [lbm.CONVERGED, lbm.CONVERGED]
+    with lbm.Batch(inst, collision="mrt") as c:
+        c.init()
+        c.step(int(max(steps)) + 20000)
+        c.observe()
+        _, _, _, ref = c.results()
+    assert obs["rho_center"][0] == pytest.approx(ref["rho_center"][0], rel=1e-4)
+    assert obs["rho_corner"][0] == pytest.approx(ref["rho_corner"][0], rel=1e-3)
+    assert obs["rho_row_mid"][1] == pytest.approx(ref["rho_row_mid"][1], rel=1e-4)
+    assert obs["rho_row0"][1] == pytest.approx(ref["rho_row0"][1], rel=1e-3)
+
+
 def test_graph_intervals_equal_plain_steps(lbm):
     inst = instances()
     with lbm.Batch(inst) as a, lbm.Batch(inst) as c:
