@@ -244,13 +244,35 @@ typedef struct lbm_batch lbm_batch;
 int lbm_batch_create(const lbm_batch_params *bp, const lbm_instance *inst, int n, lbm_batch **out);
 void lbm_batch_destroy(lbm_batch *b);
 
-/* Initial state of every instance from its preset (computed on the device),
- * or, for instances with use_profile_host[i] != 0, from a density profile:
- * profiles_dev is a device array [n][nb] of densities at s_k = (k + 1/2)
- * smax/nb, s = r/R (droplet, bubble) or |y - ny/2|/h (slab), linearly
- * interpolated and clamped at the ends (the learned warm start).  Pass
- * profiles_dev = NULL for presets only.  Resets steps, states and snapshots. */
-int lbm_batch_init(lbm_batch *b, const double *profiles_dev, const int32_t *use_profile_host, int nb, double smax);
+/* Initial state of every instance from its preset (computed on the device):
+ * f_a = w_a rho0, the plain method's start at rest.  Resets steps, states
+ * and snapshots. */
+int lbm_batch_init(lbm_batch *b);
+
+/* Where the nb samples of an instance's radial density profile sit: sample k
+ * at distance r_k = |centre + spacing (k - (nb - 1)/2)| from the lattice
+ * centre (droplet, bubble) or from the mid-row y = ny/2 (slab), so the grid
+ * can be centred on the interface (centre = the radius or half-width) with a
+ * spacing in lattice units.  use = 0 skips the instance (lbm_batch_init_profiles
+ * gives it its preset). */
+typedef struct {
+    int32_t use, reserved;
+    double centre, spacing;
+} lbm_profile_geom;
+
+#define LBM_INIT_REST 1   /* populations at rest: f_a = f_a^eq(rho0, -F/(2 rho0)) */
+
+/* Initial state of the instances with geom_host[i].use != 0 from a density
+ * profile (the learned warm start): profiles_dev is a device array [n][nb] of
+ * densities on the grids geom_host[i], interpolated linearly in r and held
+ * at the end values beyond them; the other instances get their preset.
+ * flags & LBM_INIT_REST: the profile instances start from the equilibrium at
+ * the velocity u = -F/(2 rho0), so that v = u + F/(2 rho) is zero and the
+ * Guo (Eq. 23) forcing meets a fluid at rest; F is the Eq. 6 force of rho0,
+ * computed as in the time step.  Otherwise f_a = w_a rho0.  Resets steps,
+ * states and snapshots. */
+int lbm_batch_init_profiles(lbm_batch *b, const double *profiles_dev, int nb, const lbm_profile_geom *geom_host,
+                            int flags);
 
 /* nsteps time steps of every running instance (no convergence checks). */
 int lbm_batch_step(lbm_batch *b, int64_t nsteps);
@@ -278,11 +300,14 @@ int lbm_batch_results(lbm_batch *b, int32_t *state, int32_t *code, int64_t *step
 /* FP64 density field of instance i (ny*nx, host). */
 int lbm_batch_read_density(lbm_batch *b, int i, double *rho_host);
 
-/* Radial density profiles of every instance, host array [n][nb]: at s_k =
- * (k + 1/2) smax/nb the mean over 64 directions of the bilinearly interpolated
- * density at distance s R from the lattice centre (droplet, bubble), or the mean
- * over x and both sides at y = ny/2 +- s h (slab). */
-int lbm_batch_profiles(lbm_batch *b, int nb, double smax, double *prof_host);
+/* Radial density profiles of every instance, host array [n][nb], on the
+ * sample grids geom_host[i] (see lbm_profile_geom; every entry is used): at
+ * r_k the mean over 64 directions of the bilinearly interpolated density at
+ * distance r_k from the lattice centre (droplet, bubble), or the mean over x
+ * and both sides of y = ny/2 +- r_k (slab); r_k is held at most half the
+ * period minus one (min(nx, ny)/2 - 1, or ny/2 - 1 for a slab), so samples
+ * past it repeat the farthest point rather than wrap onto the next image. */
+int lbm_batch_profiles(lbm_batch *b, int nb, const lbm_profile_geom *geom_host, double *prof_host);
 
 /* Tile shape of the batched step: row stages per warp (3 or 4) and rows per
  * work item; lbm_batch_autotune times the candidates (stages 3, 4 x rows 32,

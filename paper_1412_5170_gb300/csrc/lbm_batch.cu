@@ -3,7 +3,7 @@
 // items, check intervals are captured in CUDA graphs, and convergence and
 // failure are decided per instance on the device.  Also the warm-start
 // helpers: radial density profiles of instances and initial fields built
-// from a profile.
+// from a profile, optionally with the populations at rest.
 //
 // Layout: all instances' FP32-deviation populations live in two buffers,
 // instance i at element offset off_i with its own [9][ny][nx] block; FP64
@@ -297,69 +297,144 @@ __device__ __forceinline__ double preset_distance(const BInst* I, int x, int y)
     return hypot(x - I->nx / 2.0, y - I->ny / 2.0) - I->size;
 }
 
-// Initial state of every instance: rho0 from its preset (tanh profile plus
-// SplitMix64 noise), or, where prof != NULL and prof_on[i], from a profile
-// rho(s) sampled at s_k = (k + 1/2) smax / nb, s = r / R (droplet, bubble) or
-// |y - ny/2| / h (slab), linearly interpolated and clamped at the ends.
-// Then f_a = w_a rho0 stored as pull-convention deviations.
-__global__ void k_init_batch(const BInst* __restrict__ inst, int n_inst, float* __restrict__ f,
-                             const double* __restrict__ prof, const int* __restrict__ prof_on, int nb, double smax)
+// Grid of an instance's radial profile (mirrors lbm_profile_geom): sample k
+// at signed position centre + spacing (k - (nb - 1)/2) from the centre / mid-row.
+struct BGeom { int use, pad; double centre, spacing; };
+
+// Distance of node (x, y) from the centre of a droplet or bubble, or from the
+// mid-row of a slab.
+__device__ __forceinline__ double radial_distance(const BInst* I, int x, int y)
+{
+    if (I->kind == LBM_SLAB) return fabs(y - I->ny / 2.0);
+    return hypot(x - I->nx / 2.0, y - I->ny / 2.0);
+}
+
+// Profile density at distance r: linear between samples, end values beyond.
+__device__ __forceinline__ double profile_at(const double* p, int nb, const BGeom& g, double r)
+{
+    const double u = (r - g.centre) / g.spacing + 0.5 * (nb - 1);
+    if (!(u > 0.0)) return p[0];
+    if (u >= nb - 1) return p[nb - 1];
+    const int k0 = int(u);
+    const double t = u - k0;
+    return p[k0] + t * (p[k0 + 1] - p[k0]);
+}
+
+// Initial density rho0 of every instance into the FP64 node array: its
+// preset (tanh profile plus SplitMix64 noise) or, where geom[i].use, its
+// radial profile.
+__global__ void k_rho0_batch(const BInst* __restrict__ inst, int n_inst, double* __restrict__ rho0,
+                             const double* __restrict__ prof, const BGeom* __restrict__ geom, int nb)
 {
     const int i = blockIdx.y;
     if (i >= n_inst) return;
     const BInst* I = inst + i;
     const int nx = I->nx, ny = I->ny;
     const size_t n = (size_t)nx * ny;
+    const bool use_prof = prof && geom[i].use;
     for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < n; id += (size_t)gridDim.x * blockDim.x) {
         const int x = int(id % nx), y = int(id / nx);
-        auto rho0_at = [&](int xs, int ys) {
-            double r;
-            if (prof && prof_on[i]) {
-                double s;
-                if (I->kind == LBM_SLAB) s = fabs(ys - ny / 2.0) / I->size;
-                else s = hypot(xs - nx / 2.0, ys - ny / 2.0) / I->size;
-                const double u = s * nb / smax - 0.5;
-                const int k0 = int(floor(u));
-                const double t = u - k0;
-                const double* p = prof + (size_t)i * nb;
-                if (k0 < 0) r = p[0];
-                else if (k0 >= nb - 1) r = p[nb - 1];
-                else r = p[k0] + t * (p[k0 + 1] - p[k0]);
-            } else {
-                const double d = preset_distance(I, xs, ys);
-                const double in = 0.5 * (1.0 - tanh(2.0 * d / I->width));
-                r = (I->kind == LBM_BUBBLE) ? I->rho_l + (I->rho_v - I->rho_l) * in
-                                            : I->rho_v + (I->rho_l - I->rho_v) * in;
-                if (I->noise_amp != 0.0) {
-                    const unsigned long long z = splitmix64_dev(I->seed ^ (unsigned long long)((size_t)ys * nx + xs));
-                    r += I->noise_amp * (2.0 * (double(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0);
-                }
+        double r;
+        if (use_prof) {
+            r = profile_at(prof + (size_t)i * nb, nb, geom[i], radial_distance(I, x, y));
+        } else {
+            const double d = preset_distance(I, x, y);
+            const double in = 0.5 * (1.0 - tanh(2.0 * d / I->width));
+            r = (I->kind == LBM_BUBBLE) ? I->rho_l + (I->rho_v - I->rho_l) * in
+                                        : I->rho_v + (I->rho_l - I->rho_v) * in;
+            if (I->noise_amp != 0.0) {
+                const unsigned long long z = splitmix64_dev(I->seed ^ (unsigned long long)((size_t)y * nx + x));
+                r += I->noise_amp * (2.0 * (double(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0);
             }
-            return r;
+        }
+        rho0[I->node_off + id] = r;
+    }
+}
+
+// Rest velocity u0 = -F/(2 rho0) of the profile instances (into the vx, vy
+// slots of the per-node snapshot array): psi and the Eq. 6 force of rho0 in
+// the instance's compute type, exactly as the time step evaluates them.
+__global__ void k_rest_velocity(const BInst* __restrict__ inst, int n_inst, const double* __restrict__ rho0,
+                                const BGeom* __restrict__ geom, Snap* __restrict__ u0)
+{
+    const int i = blockIdx.y;
+    if (i >= n_inst || !geom[i].use) return;
+    const BInst* I = inst + i;
+    const int nx = I->nx, ny = I->ny;
+    const size_t n = (size_t)nx * ny;
+    const Coef<float> k = I->k;
+    const double* r0 = rho0 + I->node_off;
+    for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < n; id += (size_t)gridDim.x * blockDim.x) {
+        const int x = int(id % nx), y = int(id / nx);
+        unsigned bad = 0;
+        auto psi_at = [&](int dx, int dy) {
+            const int xs = wrap_any(x + dx, nx), ys = wrap_any(y + dy, ny);
+            const float drho = float(r0[(size_t)ys * nx + xs] - double(k.rho_ref));
+            return psi_of_rho<float>(k.rho_ref + drho, k, bad);
         };
+        const Stencil<float> q{psi_at(0, 0), psi_at(1, 0), psi_at(0, 1), psi_at(-1, 0), psi_at(0, -1),
+                               psi_at(1, 1), psi_at(-1, 1), psi_at(-1, -1), psi_at(1, -1)};
+        float Fx, Fy;
+        force<float>(q, k, Fx, Fy);
+        const float rho = k.rho_ref + float(r0[id] - double(k.rho_ref));
+        Snap& o = u0[I->node_off + id];
+        o.vx = -0.5f * Fx / rho;
+        o.vy = -0.5f * Fy / rho;
+    }
+}
+
+// Populations from rho0 (and, for the rest-started instances, u0) as
+// pull-convention FP32 deviations: the value stored at x for direction a is
+// the one that arrives at x + e_a, f_a = w_a rho0 (1 + 3 e.u + 9/2 (e.u)^2 -
+// 3/2 u.u) there (Eq. 2 with c_s^2 = 1/3), minus w_a rho_ref.
+__global__ void k_pops_batch(const BInst* __restrict__ inst, int n_inst, float* __restrict__ f,
+                             const double* __restrict__ rho0, const Snap* __restrict__ u0,
+                             const BGeom* __restrict__ geom)
+{
+    const int i = blockIdx.y;
+    if (i >= n_inst) return;
+    const BInst* I = inst + i;
+    const int nx = I->nx, ny = I->ny;
+    const size_t n = (size_t)nx * ny;
+    const double* r0 = rho0 + I->node_off;
+    const bool rest = u0 && geom && geom[i].use;
+    for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < n; id += (size_t)gridDim.x * blockDim.x) {
+        const int x = int(id % nx), y = int(id / nx);
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
             const int xs = ex(a) > 0 ? inc1(x, nx) : (ex(a) < 0 ? dec1(x, nx) : x);
             const int ys = ey(a) > 0 ? inc1(y, ny) : (ey(a) < 0 ? dec1(y, ny) : y);
-            const double w = wt<double>(a);
-            f[I->off + a * n + id] = float(w * rho0_at(xs, ys) - w * double(I->k.rho_ref));
+            const size_t src = (size_t)ys * nx + xs;
+            const double w = wt<double>(a), r = r0[src];
+            double v = w * r - w * double(I->k.rho_ref);
+            if (rest) {
+                const Snap u = u0[I->node_off + src];
+                const double ux = u.vx, uy = u.vy;
+                const double eu = ex(a) * ux + ey(a) * uy;
+                v += w * r * (3.0 * eu + 4.5 * eu * eu - 1.5 * (ux * ux + uy * uy));
+            }
+            f[I->off + a * n + id] = float(v);
         }
     }
 }
 
-// Radial density profile of instance i from its FP64 density field: at
-// s_k = (k + 1/2) smax / nb, the mean over 64 directions of the bilinearly
-// interpolated (periodic) density at distance s R from the centre
-// (droplet, bubble), or the mean over x and both sides of the linearly
-// interpolated density at y = ny/2 +- s h (slab).
-__global__ void k_radial_profile(const BInst* __restrict__ inst, const double* __restrict__ rho, int nb, double smax,
-                                 double* __restrict__ prof)
+// Radial density profile of instance i from its FP64 density field on its
+// sample grid: at r_k = |centre + spacing (k - (nb - 1)/2)| the mean over 64
+// directions of the bilinearly interpolated density at distance r_k from the
+// centre (droplet, bubble), or the mean over x and both sides of the
+// mid-row at y = ny/2 +- r_k (slab), with r_k held at most half the period
+// minus one.  One block per (sample, instance).
+__global__ void k_radial_profile(const BInst* __restrict__ inst, const double* __restrict__ rho, int nb,
+                                 const BGeom* __restrict__ geom, double* __restrict__ prof)
 {
     const int i = blockIdx.y, kb = blockIdx.x;
     const BInst* I = inst + i;
     const int nx = I->nx, ny = I->ny;
     const double* r = rho + I->node_off;
-    const double s = (kb + 0.5) * smax / nb;
+    // Distances beyond the half period would wrap onto the next image of the
+    // droplet or slab: they are held at the farthest point of the period.
+    const double rmax = (I->kind == LBM_SLAB ? ny : min(nx, ny)) / 2.0 - 1.0;
+    const double dist = fmin(fabs(geom[i].centre + geom[i].spacing * (kb - 0.5 * (nb - 1))), rmax);
     __shared__ double acc[128];
     double sum = 0;
     int cnt = 0;
@@ -367,7 +442,7 @@ __global__ void k_radial_profile(const BInst* __restrict__ inst, const double* _
     if (I->kind == LBM_SLAB) {
         for (int x = threadIdx.x; x < nx; x += blockDim.x) {
             for (int side = -1; side <= 1; side += 2) {
-                const double yy = ny / 2.0 + side * s * I->size;
+                const double yy = ny / 2.0 + side * dist;
                 const int y0 = int(floor(yy));
                 const double t = yy - y0;
                 sum += (1 - t) * at(x, y0) + t * at(x, y0 + 1);
@@ -377,7 +452,7 @@ __global__ void k_radial_profile(const BInst* __restrict__ inst, const double* _
     } else {
         for (int d = threadIdx.x; d < 64; d += blockDim.x) {
             const double th = 2.0 * 3.14159265358979323846 * d / 64;
-            const double xx = nx / 2.0 + s * I->size * cos(th), yy = ny / 2.0 + s * I->size * sin(th);
+            const double xx = nx / 2.0 + dist * cos(th), yy = ny / 2.0 + dist * sin(th);
             const int x0 = int(floor(xx)), y0 = int(floor(yy));
             const double tx = xx - x0, ty = yy - y0;
             sum += (1 - tx) * (1 - ty) * at(x0, y0) + tx * (1 - ty) * at(x0 + 1, y0) +
@@ -737,21 +812,61 @@ static int reset_run_state(lbm_batch* b)
     return build_items(b, nullptr);
 }
 
-int lbm_batch_init(lbm_batch* b, const double* profiles_dev, const int32_t* use_profile_host, int nb, double smax)
+// Copy n profile grids to the device (caller frees); nullptr on failure.
+static BGeom* device_geom(lbm_batch* b, const lbm_profile_geom* g)
 {
-    if (!b || (profiles_dev && (!use_profile_host || nb < 2 || !(smax > 0)))) return LBM_E_INVALID;
+    std::vector<BGeom> h(b->n);
+    for (int i = 0; i < b->n; ++i) h[i] = BGeom{g[i].use ? 1 : 0, 0, g[i].centre, g[i].spacing};
+    BGeom* d = nullptr;
+    if (cudaMalloc(&d, sizeof(BGeom) * b->n) != cudaSuccess) return nullptr;
+    if (cudaMemcpyAsync(d, h.data(), sizeof(BGeom) * b->n, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        cudaFree(d);
+        return nullptr;
+    }
+    return d;
+}
+
+// rho0 into the FP64 node array, then (rest) u0 into the snapshot array's
+// velocity slots, then the populations; the snapshot is cleared again after.
+static int init_fields(lbm_batch* b, const double* prof, int nb, const BGeom* dgeom, bool rest)
+{
     int s = reset_run_state(b);
     if (s != LBM_OK) return s;
-    int* on = nullptr;
-    if (profiles_dev) {
-        B_CUDA(cudaMalloc(&on, sizeof(int) * b->n));
-        B_CUDA(cudaMemcpyAsync(on, use_profile_host, sizeof(int) * b->n, cudaMemcpyHostToDevice, b->stream));
+    const dim3 grid(64, b->n);
+    k_rho0_batch<<<grid, 256, 0, b->stream>>>(b->dinst, b->n, b->rho, prof, dgeom, nb);
+    if (rest) k_rest_velocity<<<grid, 256, 0, b->stream>>>(b->dinst, b->n, b->rho, dgeom, b->snap);
+    k_pops_batch<<<grid, 256, 0, b->stream>>>(b->dinst, b->n, b->f[0], b->rho, rest ? b->snap : nullptr,
+                                              prof ? dgeom : nullptr);
+    B_CUDA(cudaGetLastError());
+    if (rest) {
+        long long nodes = 0;
+        for (const BInst& I : b->hinst) nodes = std::max<long long>(nodes, I.node_off + (long long)I.nx * I.ny);
+        B_CUDA(cudaMemsetAsync(b->snap, 0xff, sizeof(Snap) * nodes, b->stream));   // NaN: no snapshot yet
     }
-    k_init_batch<<<dim3(64, b->n), 256, 0, b->stream>>>(b->dinst, b->n, b->f[0], profiles_dev, on, nb, smax);
-    cudaError_t e = cudaGetLastError();
-    cudaStreamSynchronize(b->stream);
-    if (on) cudaFree(on);
-    return cuda_ok(e);
+    B_CUDA(cudaStreamSynchronize(b->stream));
+    return LBM_OK;
+}
+
+int lbm_batch_init(lbm_batch* b)
+{
+    if (!b) return LBM_E_INVALID;
+    return init_fields(b, nullptr, 0, nullptr, false);
+}
+
+int lbm_batch_init_profiles(lbm_batch* b, const double* profiles_dev, int nb, const lbm_profile_geom* geom_host,
+                            int flags)
+{
+    if (!b || !profiles_dev || !geom_host || nb < 2 || nb > 4096 || (flags & ~LBM_INIT_REST)) return LBM_E_INVALID;
+    for (int i = 0; i < b->n; ++i)
+        if (geom_host[i].use && !(std::isfinite(geom_host[i].centre) && geom_host[i].spacing > 0 &&
+                                  std::isfinite(geom_host[i].spacing)))
+            return LBM_E_INVALID;
+    BGeom* dgeom = device_geom(b, geom_host);
+    if (!dgeom) return LBM_E_CUDA;
+    const int s = init_fields(b, profiles_dev, nb, dgeom, (flags & LBM_INIT_REST) != 0);
+    cudaFree(dgeom);
+    return s;
 }
 
 int lbm_batch_step(lbm_batch* b, int64_t nsteps)
@@ -840,20 +955,28 @@ int lbm_batch_read_density(lbm_batch* b, int i, double* rho_host)
     return LBM_OK;
 }
 
-int lbm_batch_profiles(lbm_batch* b, int nb, double smax, double* prof_host)
+int lbm_batch_profiles(lbm_batch* b, int nb, const lbm_profile_geom* geom_host, double* prof_host)
 {
-    if (!b || nb < 2 || nb > 1024 || !(smax > 0) || !prof_host) return LBM_E_INVALID;
+    if (!b || nb < 2 || nb > 4096 || !geom_host || !prof_host) return LBM_E_INVALID;
+    for (int i = 0; i < b->n; ++i)
+        if (!(std::isfinite(geom_host[i].centre) && std::isfinite(geom_host[i].spacing))) return LBM_E_INVALID;
+    BGeom* dgeom = device_geom(b, geom_host);
+    if (!dgeom) return LBM_E_CUDA;
     double* dprof = nullptr;
-    B_CUDA(cudaMalloc(&dprof, sizeof(double) * nb * b->n));
+    if (cudaMalloc(&dprof, sizeof(double) * nb * b->n) != cudaSuccess) {
+        cudaFree(dgeom);
+        return LBM_E_CUDA;
+    }
     int s = observe(b, BO_RHO | BO_ALL, 0, 0, 0, 0);
     if (s == LBM_OK) {
-        k_radial_profile<<<dim3(nb, b->n), 128, 0, b->stream>>>(b->dinst, b->rho, nb, smax, dprof);
+        k_radial_profile<<<dim3(nb, b->n), 128, 0, b->stream>>>(b->dinst, b->rho, nb, dgeom, dprof);
         s = cuda_ok(cudaGetLastError());
     }
     if (s == LBM_OK)
         s = cuda_ok(cudaMemcpyAsync(prof_host, dprof, sizeof(double) * nb * b->n, cudaMemcpyDeviceToHost, b->stream));
     const cudaError_t e = cudaStreamSynchronize(b->stream);
     cudaFree(dprof);
+    cudaFree(dgeom);
     if (s != LBM_OK) return s;
     return cuda_ok(e);
 }

@@ -56,6 +56,11 @@ class lbm_batch_params(ctypes.Structure):
                 ("s_q", ctypes.c_double)]
 
 
+class lbm_profile_geom(ctypes.Structure):
+    _fields_ = [("use", ctypes.c_int32), ("reserved", ctypes.c_int32), ("centre", ctypes.c_double),
+                ("spacing", ctypes.c_double)]
+
+
 class lbm_instance(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("kind", ctypes.c_int32), ("cell", ctypes.c_int32),
                 ("T_over_Tc", ctypes.c_double), ("tau", ctypes.c_double), ("A", ctypes.c_double),
@@ -73,6 +78,7 @@ BATCH_NOBS = 10
 BATCH_OBS = ("mass", "max_v", "max_dv", "max_drho", "rho_min", "rho_max", "rho_center", "rho_corner",
              "rho_row_mid", "rho_row0")
 RUNNING, CONVERGED, FAILED = 0, 1, 2
+LBM_INIT_REST = 1
 
 _vp, _dp, _i64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64
 _PROTOS = {
@@ -106,14 +112,15 @@ _PROTOS = {
     "lbm_batch_create": (ctypes.c_int, [ctypes.POINTER(lbm_batch_params), ctypes.POINTER(lbm_instance), ctypes.c_int,
                                         ctypes.POINTER(_vp)]),
     "lbm_batch_destroy": (None, [_vp]),
-    "lbm_batch_init": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double]),
+    "lbm_batch_init": (ctypes.c_int, [_vp]),
+    "lbm_batch_init_profiles": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, ctypes.c_int]),
     "lbm_batch_step": (ctypes.c_int, [_vp, _i64]),
     "lbm_batch_run_to_steady": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, _i64, _i64,
                                                ctypes.POINTER(_i64)]),
     "lbm_batch_observe": (ctypes.c_int, [_vp]),
     "lbm_batch_results": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "lbm_batch_read_density": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
-    "lbm_batch_profiles": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, _vp]),
+    "lbm_batch_profiles": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "lbm_batch_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "lbm_batch_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_int), _dp]),
@@ -354,15 +361,25 @@ class Batch:
     def nodes(self) -> int:
         return int(lbm_batch_nodes(self.h))
 
-    def init(self, profiles=None, use=None, smax=2.0):
-        """Presets, or (with a torch CUDA float64 tensor profiles [n, nb] and a
-        0/1 sequence use) density profiles for the selected instances."""
-        if profiles is None:
-            check(lbm_batch_init(self.h, None, None, 0, 0.0), "lbm_batch_init")
-            return
-        nb = int(profiles.shape[1])
-        on = (ctypes.c_int32 * self.n)(*[int(bool(u)) for u in use])
-        check(lbm_batch_init(self.h, _vp(profiles.data_ptr()), on, nb, float(smax)), "lbm_batch_init")
+    def init(self):
+        """Every instance from its preset (f = w rho0)."""
+        check(lbm_batch_init(self.h), "lbm_batch_init")
+
+    def _geom(self, geom):
+        """geom: n entries of (use, centre, spacing)."""
+        arr = (lbm_profile_geom * self.n)()
+        for i, (use, centre, spacing) in enumerate(geom):
+            arr[i] = lbm_profile_geom(int(bool(use)), 0, float(centre), float(spacing))
+        return arr
+
+    def init_profiles(self, profiles, geom, rest=True):
+        """Instances with use != 0 from radial density profiles: profiles is a
+        torch CUDA float64 tensor [n, nb], geom n tuples (use, centre, spacing)
+        placing sample k at |centre + spacing (k - (nb-1)/2)|; rest: start the
+        populations at rest (v = 0) instead of f = w rho0."""
+        assert profiles.is_cuda and profiles.dtype.itemsize == 8 and profiles.is_contiguous()
+        check(lbm_batch_init_profiles(self.h, _vp(profiles.data_ptr()), int(profiles.shape[1]), self._geom(geom),
+                                      LBM_INIT_REST if rest else 0), "lbm_batch_init_profiles")
 
     def step(self, n: int):
         check(lbm_batch_step(self.h, int(n)), "lbm_batch_step")
@@ -390,9 +407,11 @@ class Batch:
         check(lbm_batch_read_density(self.h, int(i), rho.ctypes.data_as(_vp)), "lbm_batch_read_density")
         return rho
 
-    def profiles(self, nb=64, smax=2.0) -> np.ndarray:
+    def profiles(self, nb, geom) -> np.ndarray:
+        """Radial density profiles [n, nb] on the grids geom (n tuples
+        (use, centre, spacing); use is ignored)."""
         out = np.empty((self.n, nb))
-        check(lbm_batch_profiles(self.h, int(nb), float(smax), out.ctypes.data_as(_vp)), "lbm_batch_profiles")
+        check(lbm_batch_profiles(self.h, int(nb), self._geom(geom), out.ctypes.data_as(_vp)), "lbm_batch_profiles")
         return out
 
     def set_tuning(self, stages, rows):

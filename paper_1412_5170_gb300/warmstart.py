@@ -1,100 +1,271 @@
 """Learned warm start for batched runs to steady state.
 
 Training data come from the batched solver itself: instances drawn from the
-workload distribution are run to steady state and their converged density
-profiles are sampled at s_k = (k + 1/2) * 2/64, s = r/R (droplet) or
-|y - ny/2|/h (slab).  A network per geometry (inputs T/Tc, tau, A, K, radius
-or half-width; outputs log rho at the 64 samples), trained by liblbm's own
-FP32 kernels, predicts the profile of a new instance; the batched solver then
-starts from that profile instead of the tanh preset and runs to the same
-convergence criterion, so the solver itself judges the prediction (an
-instance whose warm start fails is simply rerun cold).
+workload distribution are run to steady state, and each converged density
+field is summarised by its equivalent size (the radius of a droplet, or the
+half-width of a slab, that holds the mass excess over the vapour) and 64
+samples of its radial density profile on a grid centred on the interface,
+r_k = R_eq + h (k - 31.5) with h = 0.5 / sqrt(K) lattice units (the
+interface widens as 1/sqrt(K) under the EOS rescaling of Eq. 30).  A network
+per geometry, trained by liblbm's own FP32 kernels, maps (T/Tc, tau, A, K,
+R_eq) to log rho at those samples.
+
+A warm start for a new instance:
+  1. its preset is initialised and its mass M0 read: the dynamics conserve
+     mass, so the warm field must hold M0 to reach the same steady state;
+  2. R_eq is found by iterating R_eq -> network -> plateau densities ->
+     R_eq from M0 (a few rounds; the profile depends on R_eq only through the
+     Laplace pressure);
+  3. the profile is laid on the lattice with the populations at rest
+     (lbm_batch_init_profiles with LBM_INIT_REST: v = u + F/(2 rho) = 0), and
+     its centre is corrected twice by Newton steps on the lattice mass;
+  4. the batched solver runs to the same convergence criterion as the cold
+     run, so it judges the prediction; an instance whose warm start fails is
+     rerun cold by the caller.
 
 Orchestration only: every lattice update, reduction, profile extraction and
 network evaluation runs in liblbm's CUDA kernels.
 """
 from __future__ import annotations
 
+import math
 import time
 
 import numpy as np
 
 from . import lbm
 
-NB, SMAX = 64, 2.0
+NB = 64
 KINDS = ("droplet", "slab")
 
 
-def features(inst) -> list:
-    return [inst["T_over_Tc"], inst["tau"], inst["A"], inst["K"], inst["size"]]
+def spacing(inst) -> float:
+    return 0.5 / math.sqrt(inst["K"])
 
 
-def solve(instances, collision="mrt", tol_v=0.0, tol_rho=0.0, tol_coex=1e-5, check_every=1000, max_steps=100000,
-          profiles=None, tune=True):
-    """Run a batch to steady state.  profiles: optional (n, NB) densities for
-    a warm start (rows of NaN start from the preset).  Returns a dict with
-    per-instance state, failure code, steps, observables, converged profiles,
-    and the wall time of the run (initialisation included)."""
-    import torch
-    with lbm.Batch(instances, collision=collision) as b:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        if profiles is None:
-            b.init()
-        else:
-            use = [int(np.all(np.isfinite(p))) for p in profiles]
-            dev = torch.tensor(np.nan_to_num(np.asarray(profiles, dtype=np.float64), nan=0.0), device="cuda")
-            b.init(dev, use, SMAX)
-        if tune:
-            b.autotune(3)
-        st, done = b.run_to_steady(tol_v=tol_v, tol_rho=tol_rho, tol_coex=tol_coex, check_every=check_every,
-                                   max_steps=max_steps)
-        wall = time.perf_counter() - t0
-        state, code, steps, obs = b.results()
-        prof = b.profiles(NB, SMAX)
-        nodes = b.nodes
-    return dict(status=st, steps_done=done, state=state, code=code, steps=steps, obs=obs, profiles=prof,
-                wall_s=wall, nodes=nodes)
+def shape(inst):
+    return int(inst.get("ny", inst.get("side"))), int(inst.get("nx", inst.get("side")))
+
+
+def equivalent_size(inst, mass, rho_l, rho_v) -> float:
+    """Radius (droplet) or half-width (slab) of a sharp liquid region that
+    holds the mass excess over a uniform vapour of density rho_v."""
+    ny, nx = shape(inst)
+    area = (mass - rho_v * nx * ny) / (rho_l - rho_v)
+    if inst["kind"] == "slab":
+        return area / (2.0 * nx)
+    return math.sqrt(max(area, 0.0) / math.pi)
+
+
+def size_slope(inst, size, rho_l, rho_v) -> float:
+    """d(mass)/d(size) of a sharp liquid region."""
+    ny, nx = shape(inst)
+    if inst["kind"] == "slab":
+        return 2.0 * nx * (rho_l - rho_v)
+    return 2.0 * math.pi * size * (rho_l - rho_v)
+
+
+def features(inst, size) -> list:
+    return [inst["T_over_Tc"], inst["tau"], inst["A"], inst["K"], size]
 
 
 def coexistence(instances, obs):
     """(rho_liquid, rho_vapour) per instance: droplet centre / corner, slab mid / edge row."""
-    rl = np.where([i["kind"] == "slab" for i in instances], obs["rho_row_mid"], obs["rho_center"])
-    rv = np.where([i["kind"] == "slab" for i in instances], obs["rho_row0"], obs["rho_corner"])
+    slab = np.array([i["kind"] == "slab" for i in instances])
+    rl = np.where(slab, obs["rho_row_mid"], obs["rho_center"])
+    rv = np.where(slab, obs["rho_row0"], obs["rho_corner"])
     return rl, rv
 
 
+def profile_value(p, centre, h, r):
+    """The library's profile interpolation (linear in r, end values beyond)."""
+    u = (r - centre) / h + 0.5 * (len(p) - 1)
+    if not u > 0:
+        return p[0]
+    if u >= len(p) - 1:
+        return p[-1]
+    k = int(u)
+    return p[k] + (u - k) * (p[k + 1] - p[k])
+
+
+def converged_geometry(instances, state, obs):
+    """Equivalent size per converged instance (NaN elsewhere) and the sample
+    grids centred on it."""
+    rl, rv = coexistence(instances, obs)
+    size = np.full(len(instances), np.nan)
+    for i, d in enumerate(instances):
+        if state[i] == lbm.CONVERGED and rl[i] > rv[i] > 0:
+            size[i] = equivalent_size(d, obs["mass"][i], rl[i], rv[i])
+    geom = [(1, s if np.isfinite(s) else d["size"], spacing(d)) for d, s in zip(instances, size)]
+    return size, geom
+
+
+def _rest_init(b, instances, prof, size, use, mass0, newton=2):
+    """Lay the profiles on the lattice with the populations at rest, the
+    centre corrected by Newton steps on the lattice mass."""
+    import torch
+    dev = torch.tensor(np.nan_to_num(prof, nan=1.0), dtype=torch.float64, device="cuda")
+    centre = np.where(use, size, [d["size"] for d in instances]).astype(np.float64)
+    h = [spacing(d) for d in instances]
+    for it in range(newton + 1):
+        b.init_profiles(dev, [(u, c, hh) for u, c, hh in zip(use, centre, h)], rest=True)
+        if it == newton:
+            break
+        b.observe()
+        m = b.results()[3]["mass"]
+        for i, d in enumerate(instances):
+            if use[i]:
+                rl = profile_value(prof[i], centre[i], h[i], 0.0)
+                slope = size_slope(d, centre[i], rl, prof[i][-1])
+                if slope > 0 and np.isfinite(m[i]):
+                    centre[i] += (mass0[i] - m[i]) / slope
+    return centre
+
+
+def solve(instances, collision="mrt", tol_v=0.0, tol_rho=0.0, tol_coex=1e-5, check_every=1000, max_steps=100000,
+          warm=None, profiles=None, sizes=None, fallback="failed", tune=True):
+    """Run a batch to steady state.
+
+    warm: a trained WarmStart (predicts every instance it has a network for);
+    or profiles / sizes: given profiles [n, NB] and equivalent sizes (rows
+    with a NaN size start from the preset), e.g. the converged profiles of a
+    cold run, to measure what a perfect prediction would give.
+
+    The solver judges every warm start: an instance that fails, or converges
+    to a different steady state than the one laid down (a single phase,
+    liquid probe below 1.5 x the vapour one, e.g. a droplet that evaporated,
+    or a liquid region whose equivalent size is off by more than half), is
+    rerun cold when fallback is "failed" or "all", and its cold result
+    replaces the warm one; with "all" so is an instance still running at
+    max_steps.  A prediction without two phases (liquid plateau below 1.5 x
+    the vapour) is not used at all.
+
+    Returns a dict with per-instance state, failure code, steps of the run
+    whose result is kept, steps_total (warm plus fallback steps: the work
+    spent), observables, the converged equivalent sizes and profiles (on
+    grids centred on them), which instances were warm-started and which fell
+    back, and the wall time of everything (initialisation, prediction, mass
+    matching and fallback runs included)."""
+    import torch
+    n = len(instances)
+    with lbm.Batch(instances, collision=collision) as b:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.init()
+        use = np.zeros(n, dtype=bool)
+        centre_used = np.full(n, np.nan)
+        if warm is not None or profiles is not None:
+            b.observe()
+            mass0 = b.results()[3]["mass"].copy()
+            if warm is not None:
+                prof, size = warm.initial_profiles(instances, mass0)
+            else:
+                prof, size = np.asarray(profiles, dtype=np.float64), np.asarray(sizes, dtype=np.float64)
+            use = np.isfinite(size) & np.all(np.isfinite(prof), axis=1) & np.all(prof > 0, axis=1)
+            # a prediction without two phases (liquid plateau < 1.5 x vapour) is not used
+            for i in np.nonzero(use)[0]:
+                if not profile_value(prof[i], size[i], spacing(instances[i]), 0.0) > 1.5 * prof[i][-1]:
+                    use[i] = False
+            if use.any():
+                centre_used = _rest_init(b, instances, prof, size, use, mass0)
+        if tune:
+            b.autotune(3)
+        st, done = b.run_to_steady(tol_v=tol_v, tol_rho=tol_rho, tol_coex=tol_coex, check_every=check_every,
+                                   max_steps=max_steps)
+        state, code, steps, obs = b.results()
+        eq_size, geom = converged_geometry(instances, state, obs)
+        prof_out = b.profiles(NB, geom)
+        nodes = b.nodes
+    wall = time.perf_counter() - t0
+    steps_total = steps.copy()
+    rl, rv = coexistence(instances, obs)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        # a different steady state: one phase left, or a liquid region of another size
+        off = ~(rl > 1.5 * rv) | ~(np.abs(eq_size / centre_used - 1) < 0.5)
+    redo = use & ((state == lbm.FAILED) | ((state == lbm.CONVERGED) & off) |
+                  ((state == lbm.RUNNING) & (fallback == "all")))
+    if fallback not in ("failed", "all"):
+        redo[:] = False
+    if redo.any():
+        idx = np.nonzero(redo)[0]
+        r2 = solve([instances[i] for i in idx], collision, tol_v, tol_rho, tol_coex, check_every, max_steps,
+                   tune=tune)
+        wall += r2["wall_s"]
+        state, code, steps = state.copy(), code.copy(), steps.copy()
+        obs = {k: v.copy() for k, v in obs.items()}
+        for j, i in enumerate(idx):
+            state[i], code[i], steps[i] = r2["state"][j], r2["code"][j], r2["steps"][j]
+            steps_total[i] += r2["steps"][j]
+            for k in obs:
+                obs[k][i] = r2["obs"][k][j]
+            eq_size[i] = r2["sizes"][j]
+            prof_out[i] = r2["profiles"][j]
+    return dict(status=st, steps_done=done, state=state, code=code, steps=steps, steps_total=steps_total, obs=obs,
+                sizes=eq_size, profiles=prof_out, warm=use, fallback=redo,
+                wall_s=wall, nodes=nodes)
+
+
 class WarmStart:
-    """One network per geometry, trained on converged profiles."""
+    """One network per geometry: (T/Tc, tau, A, K, R_eq) -> log rho at the
+    64 interface-centred samples."""
 
     def __init__(self, hidden=128, layers=3, seed=0):
         self.nets = {k: lbm.WarmStartNet(5, hidden, layers, NB, seed=seed + i) for i, k in enumerate(KINDS)}
+        self.trained = set()
 
-    def fit(self, instances, profiles, epochs=2000, batch=256, lr=1e-3, seed=0):
-        """Train on converged profiles (n, NB); returns the final loss per geometry."""
-        X = np.array([features(i) for i in instances], dtype=np.float32)
-        Y = np.log(np.asarray(profiles, dtype=np.float64)).astype(np.float32)
+    def fit(self, instances, profiles, sizes, epochs=3000, batch=64, lr=2e-3, seed=0, chunks=30):
+        """Train on converged profiles [n, NB] with their equivalent sizes
+        (rows with a NaN size are skipped): Adam on minibatches with the step
+        size decayed along a cosine over `chunks` stages.  Returns the final
+        loss per geometry."""
+        ok = np.isfinite(sizes) & np.all(np.asarray(profiles) > 0, axis=1)
+        X = np.array([features(d, s) for d, s in zip(instances, sizes)], dtype=np.float32)
+        Y = np.log(np.where(ok[:, None], profiles, 1.0)).astype(np.float32)
         losses = {}
+        per = max(1, epochs // chunks)
         for k, net in self.nets.items():
-            sel = np.array([i["kind"] == k for i in instances])
+            sel = ok & np.array([d["kind"] == k for d in instances])
             if sel.sum() < 2:
                 continue
             xs, ys = X[sel].std(0), Y[sel].std(0)
             xs[xs == 0] = 1.0
             ys[ys == 0] = 1.0
             net.set_scaling(X[sel].mean(0), xs, Y[sel].mean(0), ys)
-            losses[k] = net.train(X[sel], Y[sel], epochs=epochs, batch=batch, lr=lr, seed=seed)
+            for c in range(chunks):
+                step = lr * (0.5 * (1.0 + math.cos(math.pi * c / chunks)) + 1e-3)
+                losses[k] = net.train(X[sel], Y[sel], epochs=per, batch=batch, lr=step, seed=seed + c)
+            self.trained.add(k)
         return losses
 
-    def predict(self, instances) -> np.ndarray:
-        """Predicted density profiles (n, NB)."""
-        X = np.array([features(i) for i in instances], dtype=np.float32)
+    def predict(self, instances, sizes) -> np.ndarray:
+        """Predicted density profiles [n, NB] (NaN rows for untrained geometries)."""
+        X = np.array([features(d, s) for d, s in zip(instances, sizes)], dtype=np.float32)
         out = np.full((len(instances), NB), np.nan)
-        for k, net in self.nets.items():
-            sel = np.array([i["kind"] == k for i in instances])
+        for k in self.trained:
+            sel = np.array([d["kind"] == k for d in instances])
             if sel.any():
-                out[sel] = np.exp(net.predict(X[sel]).astype(np.float64))
+                out[sel] = np.exp(self.nets[k].predict(X[sel]).astype(np.float64))
         return out
+
+    def initial_profiles(self, instances, mass0, rounds=3):
+        """Profiles and equivalent sizes consistent with the conserved masses
+        mass0: R_eq -> prediction -> plateaus -> R_eq, starting from the
+        nominal sizes."""
+        size = np.array([d["size"] for d in instances], dtype=np.float64)
+        prof = self.predict(instances, size)
+        for _ in range(rounds):
+            for i, d in enumerate(instances):
+                p = prof[i]
+                if not np.all(np.isfinite(p)):
+                    continue
+                rl = profile_value(p, size[i], spacing(d), 0.0)
+                rv = p[-1]
+                if rl > rv > 0:
+                    size[i] = equivalent_size(d, mass0[i], rl, rv)
+            prof = self.predict(instances, size)
+        bad = ~np.all(np.isfinite(prof), axis=1)
+        size[bad] = np.nan
+        return prof, size
 
     def close(self):
         for n in self.nets.values():

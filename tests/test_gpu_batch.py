@@ -118,24 +118,69 @@ def test_graph_intervals_equal_plain_steps(lbm):
 
 
 def test_profiles_of_initial_fields_and_profile_init(lbm):
-    """Radial profile of a fresh tanh droplet follows the tanh law; a field
-    built from a profile reproduces it."""
+    """Radial profile of a fresh tanh droplet / slab on an interface-centred
+    grid follows the tanh law; a field built from a profile reproduces it."""
     import torch
     inst = [dict(side=128, kind="droplet", T_over_Tc=0.8, tau=1.0, A=-0.304, K=1.0, size=30.0, seed=8, noise_amp=0.0),
             dict(nx=16, ny=128, kind="slab", T_over_Tc=0.8, tau=1.0, A=-0.304, K=1.0, size=25.0, seed=9, noise_amp=0.0)]
     rv, rl = lbm.maxwell(0.8)
-    nb, smax = 64, 2.0
-    s = (np.arange(nb) + 0.5) * smax / nb
+    nb, h = 64, 0.5
+    geom = [(1, d["size"], h) for d in inst]
     with lbm.Batch(inst) as b:
         b.init()
-        prof = b.profiles(nb, smax)
+        prof = b.profiles(nb, geom)
         for i, d in enumerate(inst):
-            want = rv + (rl - rv) * 0.5 * (1 - np.tanh(2 * (s * d["size"] - d["size"]) / 4.0))
+            r = np.abs(d["size"] + h * (np.arange(nb) - 31.5))
+            want = rv + (rl - rv) * 0.5 * (1 - np.tanh(2 * (r - d["size"]) / 4.0))
             assert np.abs(prof[i] - want).max() < 0.02 * (rl - rv)
         dev = torch.tensor(prof, dtype=torch.float64, device="cuda")
-        b.init(dev, [1, 1], smax)
-        prof2 = b.profiles(nb, smax)
+        b.init_profiles(dev, geom, rest=False)
+        prof2 = b.profiles(nb, geom)
     assert np.abs(prof2 - prof).max() < 0.02 * (rl - rv)
+
+
+def _profile_field(d, p, centre, h):
+    """rho0 of a profile laid on an instance (the library's interpolation)."""
+    ny, nx = d.get("ny", d.get("side")), d.get("nx", d.get("side"))
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    r = np.abs(y - ny / 2.0) if d["kind"] == "slab" else np.hypot(x - nx / 2.0, y - ny / 2.0)
+    u = (r - centre) / h + 0.5 * (len(p) - 1)
+    k = np.clip(np.floor(u).astype(int), 0, len(p) - 2)
+    t = u - k
+    out = p[k] + t * (p[k + 1] - p[k])
+    out = np.where(u > 0, out, p[0])
+    return np.where(u >= len(p) - 1, p[-1], out)
+
+
+def test_profile_init_at_rest(lbm):
+    """LBM_INIT_REST: the populations carry momentum -F/2, so the observed
+    velocity v = u + F/(2 rho) starts at zero up to FP32 rounding, while the
+    plain start f = w rho0 has v = F/(2 rho) at the interface; the density
+    is the profile's either way."""
+    import torch
+    inst = [dict(side=96, kind="droplet", T_over_Tc=0.75, tau=0.9, A=-0.5, K=0.7, size=20.0, seed=1),
+            dict(nx=32, ny=96, kind="slab", T_over_Tc=0.8, tau=0.8, A=-0.5, K=1.0, size=18.0, seed=2)]
+    nb, h = 64, 0.5
+    rv, rl = lbm.maxwell(0.75)
+    prof = np.empty((2, nb))
+    geom = []
+    for i, d in enumerate(inst):
+        r = np.abs(d["size"] + h * (np.arange(nb) - 31.5))
+        prof[i] = rv + (rl - rv) * 0.5 * (1 - np.tanh(2 * (r - d["size"]) / 5.0))
+        geom.append((1, d["size"], h))
+    dev = torch.tensor(prof, dtype=torch.float64, device="cuda")
+    out = {}
+    with lbm.Batch(inst, collision="mrt") as b:
+        for rest in (False, True):
+            b.init_profiles(dev, geom, rest=rest)
+            b.observe()
+            out[rest] = b.results()[3]["max_v"].copy()
+            for i, d in enumerate(inst):
+                want = _profile_field(d, prof[i], d["size"], h)
+                got = b.read_density(i)
+                assert np.abs(got - want).max() < 1e-6 * want.max()
+    assert np.all(out[False] > 1e-4)
+    assert np.all(out[True] < 1e-6) and np.all(out[True] < 1e-3 * out[False])
 
 
 def test_batch_autotune_keeps_state(lbm):
