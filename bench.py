@@ -38,10 +38,14 @@ MRT = dict(s_e=0.8, s_eps=0.8, s_q=1.1)
 BYTES_PER_NODE = 72          # 9 FP32 deviations read + 9 written
 SEED = 20141217 + 2 * 1000
 
-# DRAM bytes (read + write) per launch of the strip kernel measured by ncu on
-# the workload above, keyed by the sha256 of the kernel sources it was taken
-# from; when the sources change the entry no longer matches and traffic is null.
-TRAFFIC_CAPTURES: dict = {}
+# DRAM bytes (read + write) per launch of the step kernel measured by ncu on
+# the workload above (mean of three launches), keyed by the sha256 of the
+# kernel sources it was taken from, the kernel configuration id and the
+# lattice side; when any of them changes the entry no longer matches and
+# traffic is null.
+TRAFFIC_CAPTURES: dict = {
+    ("a415cf571ec8d26d", 1, 4096): (620.04e6 + 550.94e6),
+}
 KERNEL_SOURCES = ["paper_1412_5170_gb300/csrc/lbm_warp.cuh", "paper_1412_5170_gb300/csrc/lbm_strip.cuh",
                   "paper_1412_5170_gb300/csrc/lbm_strip_f32.cu",
                   "paper_1412_5170_gb300/csrc/lbm_device.cuh",
@@ -289,7 +293,7 @@ def run_ours(args):
     if rank == 0:
         peak, peak_kind = measured_peaks()
         achieved = BYTES_PER_NODE * nodes / (kernel_ms * 1e-3) / 1e9
-        traffic = TRAFFIC_CAPTURES.get(kernel_hash())
+        traffic = TRAFFIC_CAPTURES.get((kernel_hash(), chosen[0], N_SIDE))
         cpu_steps = args.cpu_steps
         cpu_rate, cpu_el = cpu_oracle_rate(cpu_steps, CELL, SEED) if cpu_steps > 0 else (None, 0.0)
         line = {
@@ -305,7 +309,8 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": "%s (hbm_gbs, copy)" % peak_kind,
                          "kernel": kernel_name(chosen), "kernel_ms": kernel_ms,
-                         "bytes_per_node": BYTES_PER_NODE},
+                         "bytes_per_node": BYTES_PER_NODE, "algorithmic_bytes": BYTES_PER_NODE * nodes,
+                         "traffic_unit": "DRAM bytes read + written per launch (ncu)"},
             "cpu_baseline": {"value": cpu_rate, "unit": "MLUPS", "cores": 1, "kind": "oracle",
                              "sample": "%d FP64 oracle steps on one 256x256 droplet cell (%.1f s)"
                                        % (cpu_steps, cpu_el)},
