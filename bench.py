@@ -396,6 +396,13 @@ def run_warmstart(args):
     def stats(x):
         return None if len(x) == 0 else {"median": float(np.median(x)), "mean": float(np.mean(x))}
 
+    # Wall time to steady state on the instances both runs solve (the batch's
+    # wall time is otherwise set by the instances neither run converges
+    # within max_steps): both runs again on that subset alone.
+    sub_inst = [test[i] for i in np.nonzero(both)[0]]
+    cold_sub = ws.solve(sub_inst, **crit)
+    warm_sub = ws.solve(sub_inst, warm=net, **crit)
+
     # instances whose warm and cold steady states differ by more than 1 %
     odd = [dict(i=int(i), kind=test[i]["kind"], side=test[i]["side"], size=round(test[i]["size"], 2),
                 T=round(test[i]["T_over_Tc"], 3), K=round(test[i]["K"], 3), tau=round(test[i]["tau"], 3),
@@ -408,8 +415,26 @@ def run_warmstart(args):
         "cold_steps": stats(cold["steps"][both]),
         "warm_over_cold_steps": stats(warm["steps_total"][both] / cold["steps"][both]),
         "perfect_profile_steps": stats(ceil["steps_total"][both & conv(ceil)]),
-        "fallbacks": {"warm": int(warm["fallback"].sum()), "perfect_profile": int(ceil["fallback"].sum())},
+        "fallbacks": {"warm": int(warm["fallback"].sum()), "perfect_profile": int(ceil["fallback"].sum()),
+                      "warm_failed": int((warm["first"]["state"] == lbm.FAILED).sum()),
+                      "warm_other_state": int(warm["first"]["off"].sum()),
+                      "predicted_uniform": int(warm["first"]["uniform"].sum()),
+                      "predicted_uniform_cold_single_phase": int(np.sum(warm["first"]["uniform"] &
+                                                                        ~(rl_c > 1.5 * rv_c))),
+                      "warm_detail": [dict(i=int(i), kind=test[i]["kind"], side=test[i]["side"],
+                                           size=round(test[i]["size"], 1), T=round(test[i]["T_over_Tc"], 3),
+                                           K=round(test[i]["K"], 3), tau=round(test[i]["tau"], 3),
+                                           state=int(warm["first"]["state"][i]), code=int(warm["first"]["code"][i]),
+                                           steps=int(warm["first"]["steps"][i]),
+                                           rho=[float(warm["first"]["rho_l"][i]), float(warm["first"]["rho_v"][i])],
+                                           size_eq=float(warm["first"]["size"][i]),
+                                           centre=float(warm["first"]["centre"][i]),
+                                           cold=[float(rl_c[i]), float(rv_c[i]), int(cold["steps"][i])])
+                                      for i in np.nonzero(warm["fallback"])[0]]},
         "different_steady_state": odd,
+        "wall_s_converged_set": {"cold": cold_sub["wall_s"], "warm": warm_sub["wall_s"],
+                                 "instances": len(sub_inst),
+                                 "cold_converged": int(conv(cold_sub).sum()), "warm_converged": int(conv(warm_sub).sum())},
         "wall_s": {"cold_batch": cold["wall_s"], "warm_batch": warm["wall_s"], "perfect_profile_batch": ceil["wall_s"],
                    "train_data": gen["wall_s"], "training": train_s, "fp64_plain_projected": fp64_projected,
                    "total": time.perf_counter() - t0},

@@ -8,7 +8,11 @@ samples of its radial density profile on a grid centred on the interface,
 r_k = R_eq + h (k - 31.5) with h = 0.5 / sqrt(K) lattice units (the
 interface widens as 1/sqrt(K) under the EOS rescaling of Eq. 30).  A network
 per geometry, trained by liblbm's own FP32 kernels, maps (T/Tc, tau, A, K,
-R_eq) to log rho at those samples.
+R_eq) to those samples as log rho normalised by the Maxwell densities of the
+temperature (Eq. 19, liblbm's host solver): y = (log rho - log rho_v^M) /
+(log rho_l^M - log rho_v^M), about 0 in the vapour and 1 in the liquid, so the
+network learns the departure from the equal-area construction rather than
+the decades over which the vapour density ranges with T/Tc.
 
 A warm start for a new instance:
   1. its preset is initialised and its mass M0 read: the dynamics conserve
@@ -69,6 +73,21 @@ def features(inst, size) -> list:
     return [inst["T_over_Tc"], inst["tau"], inst["A"], inst["K"], size]
 
 
+_MAXWELL: dict = {}
+
+
+def maxwell_logs(instances):
+    """(log rho_v^M, log rho_l^M) per instance from liblbm's Eq. 19 solver."""
+    out = np.empty((len(instances), 2))
+    for i, d in enumerate(instances):
+        T = float(d["T_over_Tc"])
+        if T not in _MAXWELL:
+            rv, rl = lbm.maxwell(T)
+            _MAXWELL[T] = (math.log(rv), math.log(rl))
+        out[i] = _MAXWELL[T]
+    return out
+
+
 def coexistence(instances, obs):
     """(rho_liquid, rho_vapour) per instance: droplet centre / corner, slab mid / edge row."""
     slab = np.array([i["kind"] == "slab" for i in instances])
@@ -89,26 +108,30 @@ def profile_value(p, centre, h, r):
 
 
 def converged_geometry(instances, state, obs):
-    """Equivalent size per converged instance (NaN elsewhere) and the sample
-    grids centred on it."""
+    """Equivalent size per converged two-phase instance (NaN elsewhere: a
+    uniform final state has no interface to learn) and the sample grids
+    centred on it."""
     rl, rv = coexistence(instances, obs)
     size = np.full(len(instances), np.nan)
     for i, d in enumerate(instances):
-        if state[i] == lbm.CONVERGED and rl[i] > rv[i] > 0:
+        if state[i] == lbm.CONVERGED and rl[i] > 1.5 * rv[i] and rv[i] > 0:   # two phases
             size[i] = equivalent_size(d, obs["mass"][i], rl[i], rv[i])
     geom = [(1, s if np.isfinite(s) else d["size"], spacing(d)) for d, s in zip(instances, size)]
     return size, geom
 
 
-def _rest_init(b, instances, prof, size, use, mass0, newton=2):
+def _rest_init(b, instances, prof, size, use, mass0, keep=None, newton=2):
     """Lay the profiles on the lattice with the populations at rest, the
-    centre corrected by Newton steps on the lattice mass."""
+    centre corrected by Newton steps on the lattice mass; `keep` instances
+    are laid down as given (flat profiles) without correction."""
     import torch
     dev = torch.tensor(np.nan_to_num(prof, nan=1.0), dtype=torch.float64, device="cuda")
-    centre = np.where(use, size, [d["size"] for d in instances]).astype(np.float64)
+    keep = np.zeros(len(instances), dtype=bool) if keep is None else keep
+    lay = use | keep
+    centre = np.where(lay, size, [d["size"] for d in instances]).astype(np.float64)
     h = [spacing(d) for d in instances]
     for it in range(newton + 1):
-        b.init_profiles(dev, [(u, c, hh) for u, c, hh in zip(use, centre, h)], rest=True)
+        b.init_profiles(dev, [(u, c, hh) for u, c, hh in zip(lay, centre, h)], rest=True)
         if it == newton:
             break
         b.observe()
@@ -131,21 +154,27 @@ def solve(instances, collision="mrt", tol_v=0.0, tol_rho=0.0, tol_coex=1e-5, che
     with a NaN size start from the preset), e.g. the converged profiles of a
     cold run, to measure what a perfect prediction would give.
 
+    When the predicted plateaus leave no mass for a liquid region (equivalent
+    size below one lattice unit) the predicted steady state is a uniform
+    vapour: the instance starts at rest at its mean density.
+
     The solver judges every warm start: an instance that fails, or converges
-    to a different steady state than the one laid down (a single phase,
-    liquid probe below 1.5 x the vapour one, e.g. a droplet that evaporated,
-    or a liquid region whose equivalent size is off by more than half), is
-    rerun cold when fallback is "failed" or "all", and its cold result
-    replaces the warm one; with "all" so is an instance still running at
-    max_steps.  A prediction without two phases (liquid plateau below 1.5 x
-    the vapour) is not used at all.
+    to a different steady state than the one laid down (one phase where two
+    were predicted -- liquid probe below 1.5 x the vapour one, e.g. a droplet
+    that evaporated --, a liquid region whose equivalent size is off by more
+    than half, or two phases where a uniform vapour was predicted), is rerun
+    cold when fallback is "failed" or "all", and its cold result replaces the
+    warm one; with "all" so is an instance still running at max_steps.  A
+    prediction without two phases (liquid plateau below 1.5 x the vapour) is
+    not used at all.
 
     Returns a dict with per-instance state, failure code, steps of the run
     whose result is kept, steps_total (warm plus fallback steps: the work
     spent), observables, the converged equivalent sizes and profiles (on
     grids centred on them), which instances were warm-started and which fell
-    back, and the wall time of everything (initialisation, prediction, mass
-    matching and fallback runs included)."""
+    back, the warm run's own outcome before any fallback (`first`), and the
+    wall time of everything (initialisation, prediction, mass matching and
+    fallback runs included)."""
     import torch
     n = len(instances)
     with lbm.Batch(instances, collision=collision) as b:
@@ -153,6 +182,7 @@ def solve(instances, collision="mrt", tol_v=0.0, tol_rho=0.0, tol_coex=1e-5, che
         t0 = time.perf_counter()
         b.init()
         use = np.zeros(n, dtype=bool)
+        uniform = np.zeros(n, dtype=bool)
         centre_used = np.full(n, np.nan)
         if warm is not None or profiles is not None:
             b.observe()
@@ -162,12 +192,19 @@ def solve(instances, collision="mrt", tol_v=0.0, tol_rho=0.0, tol_coex=1e-5, che
             else:
                 prof, size = np.asarray(profiles, dtype=np.float64), np.asarray(sizes, dtype=np.float64)
             use = np.isfinite(size) & np.all(np.isfinite(prof), axis=1) & np.all(prof > 0, axis=1)
-            # a prediction without two phases (liquid plateau < 1.5 x vapour) is not used
-            for i in np.nonzero(use)[0]:
+            # a liquid region smaller than one lattice unit holds no mass: the
+            # predicted steady state is a uniform vapour at the mean density
+            uniform = use & (size < 1.0)
+            for i in np.nonzero(uniform)[0]:
+                ny, nx = shape(instances[i])
+                prof[i] = mass0[i] / (nx * ny)
+                size[i] = instances[i]["size"]
+            # a two-phase prediction whose liquid plateau is below 1.5 x the vapour is not used
+            for i in np.nonzero(use & ~uniform)[0]:
                 if not profile_value(prof[i], size[i], spacing(instances[i]), 0.0) > 1.5 * prof[i][-1]:
                     use[i] = False
             if use.any():
-                centre_used = _rest_init(b, instances, prof, size, use, mass0)
+                centre_used = _rest_init(b, instances, prof, size, use & ~uniform, mass0, keep=uniform)
         if tune:
             b.autotune(3)
         st, done = b.run_to_steady(tol_v=tol_v, tol_rho=tol_rho, tol_coex=tol_coex, check_every=check_every,
@@ -180,8 +217,14 @@ def solve(instances, collision="mrt", tol_v=0.0, tol_rho=0.0, tol_coex=1e-5, che
     steps_total = steps.copy()
     rl, rv = coexistence(instances, obs)
     with np.errstate(invalid="ignore", divide="ignore"):
-        # a different steady state: one phase left, or a liquid region of another size
-        off = ~(rl > 1.5 * rv) | ~(np.abs(eq_size / centre_used - 1) < 0.5)
+        # a different steady state than the one laid down: one phase left, or a
+        # liquid region of another size (two phases predicted); two phases
+        # (uniform vapour predicted)
+        two = rl > 1.5 * rv
+        off = np.where(uniform, two, ~two | ~(np.abs(eq_size / centre_used - 1) < 0.5))
+    first = dict(state=state.copy(), code=code.copy(), steps=steps.copy(), off=off & (state == lbm.CONVERGED),
+                 uniform=uniform.copy(),
+                 rho_l=rl.copy(), rho_v=rv.copy(), size=eq_size.copy(), centre=centre_used.copy())
     redo = use & ((state == lbm.FAILED) | ((state == lbm.CONVERGED) & off) |
                   ((state == lbm.RUNNING) & (fallback == "all")))
     if fallback not in ("failed", "all"):
@@ -201,13 +244,13 @@ def solve(instances, collision="mrt", tol_v=0.0, tol_rho=0.0, tol_coex=1e-5, che
             eq_size[i] = r2["sizes"][j]
             prof_out[i] = r2["profiles"][j]
     return dict(status=st, steps_done=done, state=state, code=code, steps=steps, steps_total=steps_total, obs=obs,
-                sizes=eq_size, profiles=prof_out, warm=use, fallback=redo,
+                sizes=eq_size, profiles=prof_out, warm=use, fallback=redo, first=first,
                 wall_s=wall, nodes=nodes)
 
 
 class WarmStart:
-    """One network per geometry: (T/Tc, tau, A, K, R_eq) -> log rho at the
-    64 interface-centred samples."""
+    """One network per geometry: (T/Tc, tau, A, K, R_eq) -> the 64
+    interface-centred samples of the Maxwell-normalised log density."""
 
     def __init__(self, hidden=128, layers=3, seed=0):
         self.nets = {k: lbm.WarmStartNet(5, hidden, layers, NB, seed=seed + i) for i, k in enumerate(KINDS)}
@@ -220,7 +263,8 @@ class WarmStart:
         loss per geometry."""
         ok = np.isfinite(sizes) & np.all(np.asarray(profiles) > 0, axis=1)
         X = np.array([features(d, s) for d, s in zip(instances, sizes)], dtype=np.float32)
-        Y = np.log(np.where(ok[:, None], profiles, 1.0)).astype(np.float32)
+        m = maxwell_logs(instances)
+        Y = ((np.log(np.where(ok[:, None], profiles, 1.0)) - m[:, :1]) / (m[:, 1:] - m[:, :1])).astype(np.float32)
         losses = {}
         per = max(1, epochs // chunks)
         for k, net in self.nets.items():
@@ -240,11 +284,13 @@ class WarmStart:
     def predict(self, instances, sizes) -> np.ndarray:
         """Predicted density profiles [n, NB] (NaN rows for untrained geometries)."""
         X = np.array([features(d, s) for d, s in zip(instances, sizes)], dtype=np.float32)
+        m = maxwell_logs(instances)
         out = np.full((len(instances), NB), np.nan)
         for k in self.trained:
             sel = np.array([d["kind"] == k for d in instances])
             if sel.any():
-                out[sel] = np.exp(self.nets[k].predict(X[sel]).astype(np.float64))
+                y = self.nets[k].predict(X[sel]).astype(np.float64)
+                out[sel] = np.exp(m[sel, :1] + y * (m[sel, 1:] - m[sel, :1]))
         return out
 
     def initial_profiles(self, instances, mass0, rounds=3):
