@@ -26,9 +26,9 @@ _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _SO = os.path.join(_HERE, "liboracle.so")
 
 BGK, MRT = 0, 1
-GUO, EDM, SC = 0, 1, 2
+GUO, EDM, SC, LI = 0, 1, 2, 3
 _COLL = {"bgk": BGK, "mrt": MRT}
-_FORC = {"guo": GUO, "edm": EDM, "sc": SC}
+_FORC = {"guo": GUO, "edm": EDM, "sc": SC, "li": LI}
 
 OK, E_INVALID, E_NONFINITE, E_EOS_DOMAIN = 0, 1, 3, 4
 
@@ -53,7 +53,8 @@ class Params(ctypes.Structure):
                 ("collision", ctypes.c_int32), ("forcing", ctypes.c_int32),
                 ("T_over_Tc", ctypes.c_double), ("tau", ctypes.c_double),
                 ("A", ctypes.c_double), ("K", ctypes.c_double),
-                ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double), ("s_q", ctypes.c_double)]
+                ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double), ("s_q", ctypes.c_double),
+                ("sigma", ctypes.c_double)]
 
 
 _lib_handle = None
@@ -75,7 +76,7 @@ def _lib():
         lib.orc_force.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, dp, dp]
         lib.orc_mrt_matrix.argtypes = [dp]
         lib.orc_invert9.argtypes = [dp, dp]
-        lib.orc_collide_node.argtypes = [pp, dp] + [ctypes.c_double] * 5 + [dp]
+        lib.orc_collide_node.argtypes = [pp, dp] + [ctypes.c_double] * 6 + [dp]
         lib.orc_macro.argtypes = [pp, dp] + [dp] * 8
         lib.orc_step.argtypes = [pp, dp, dp]
         lib.orc_run.argtypes = [pp, dp, ctypes.c_int64]
@@ -90,9 +91,9 @@ def _ptr(a: np.ndarray):
 
 
 def params(nx, ny, T_over_Tc, tau, A, K=1.0, collision="bgk", forcing="guo",
-           s_e=1.0, s_eps=1.0, s_q=1.0) -> Params:
+           s_e=1.0, s_eps=1.0, s_q=1.0, sigma=0.0) -> Params:
     return Params(int(nx), int(ny), _COLL[collision], _FORC[forcing], float(T_over_Tc),
-                  float(tau), float(A), float(K), float(s_e), float(s_eps), float(s_q))
+                  float(tau), float(A), float(K), float(s_e), float(s_eps), float(s_q), float(sigma))
 
 
 # ---- thermodynamics (Sec. 4.1, Eqs. 7, 29, 30) ----
@@ -137,11 +138,11 @@ def invert9(M: np.ndarray) -> np.ndarray:
     return out.reshape(9, 9)
 
 
-def collide_node(p: Params, f9, rho, ux, uy, Fx, Fy) -> np.ndarray:
+def collide_node(p: Params, f9, rho, ux, uy, Fx, Fy, psi=0.0) -> np.ndarray:
     f9 = np.ascontiguousarray(f9, dtype=np.float64)
     out = np.zeros(9)
     _lib().orc_collide_node(ctypes.byref(p), _ptr(f9), float(rho), float(ux), float(uy),
-                            float(Fx), float(Fy), _ptr(out))
+                            float(Fx), float(Fy), float(psi), _ptr(out))
     return out
 
 

@@ -3,7 +3,8 @@
  * pseudo-potential D2Q9 lattice Boltzmann model of Hu, Li & Uddin,
  * "Force Method in a Pseudo-potential Lattice Boltzmann Model"
  * (arXiv:1412.5170): Kupershtokh's hybrid psi/psi^2 force, Guo / exact
- * difference / Shan-Chen forcing, BGK or MRT collision, periodic streaming.
+ * difference / Shan-Chen forcing, BGK or MRT collision, periodic streaming;
+ * and the comparison model of Li et al. (Sec. 4.3, Eqs. 31-32).
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product library may include,
  * link or call this file; it is used by tests/, by __graft_entry__.smoke()
@@ -34,6 +35,13 @@
  *     p_xy with the usual D2Q9 polynomial rows; Lambda =
  *     diag(s_rho, s_e, s_eps, s_j, s_q, s_j, s_q, 1/tau, 1/tau) with
  *     s_rho = s_j = 1 (they drop out under Guo forcing).
+ *   - Li et al.'s model (Eq. 31): BGK, the force of Eq. 4 (Eq. 6 with A = 0),
+ *     Guo's source with v replaced by v' = v + sigma F / ((tau - 1/2) psi^2)
+ *     in its second-order term; the paper's "upsilon" there is read as
+ *     (tau - 1/2) dt, the form for which the pressure tensor gives Eq. 32's
+ *     eps = -2 (alpha + 24 G sigma) / beta, i.e. eps = 16 sigma for the
+ *     Eq. 4 force (alpha = 0, beta = 3, G = -1), matching the paper's
+ *     sigma = 0.105 <-> eps = 1.68.
  */
 #include <math.h>
 #include <stdint.h>
@@ -46,17 +54,18 @@
 #define ORC_E_INVALID 1
 
 enum { ORC_BGK = 0, ORC_MRT = 1 };
-enum { ORC_GUO = 0, ORC_EDM = 1, ORC_SC = 2 };
+enum { ORC_GUO = 0, ORC_EDM = 1, ORC_SC = 2, ORC_LI = 3 };
 
 typedef struct {
     int32_t nx, ny;
     int32_t collision;   /* ORC_BGK / ORC_MRT */
-    int32_t forcing;     /* ORC_GUO / ORC_EDM / ORC_SC */
+    int32_t forcing;     /* ORC_GUO / ORC_EDM / ORC_SC / ORC_LI */
     double T_over_Tc;    /* reduced temperature */
     double tau;          /* BGK relaxation time; MRT tau_nu */
     double A;            /* Eq. 6 weight */
     double K;            /* Eq. 30 EOS scale */
     double s_e, s_eps, s_q;  /* MRT rates (Eq. 35) */
+    double sigma;        /* Li et al.'s sigma (Eq. 31), ORC_LI only */
 } orc_params;
 
 static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -207,17 +216,26 @@ static void matvec9(const double M[81], const double x[9], double y[9])
     }
 }
 
-/* ---------------- one node: collision (Eqs. 1, 20-23, 34) ----------------
+/* ---------------- one node: collision (Eqs. 1, 20-23, 31, 34) ----------------
  * f: post-streaming populations at the node; rho, ux, uy: Eq. 3 moments
- * (u = sum f e / rho); Fx, Fy: Eq. 6 force.  Writes the post-collision
+ * (u = sum f e / rho); Fx, Fy: Eq. 6 force; psi: Eq. 7 effective density at
+ * the node (used by Li et al.'s model only).  Writes the post-collision
  * populations to fstar. */
 void orc_collide_node(const orc_params *p, const double f[9], double rho, double ux, double uy,
-                      double Fx, double Fy, double fstar[9])
+                      double Fx, double Fy, double psi, double fstar[9])
 {
     double tau = p->tau;
     double feq[9], S[9];
     if (p->collision == ORC_BGK) {
-        if (p->forcing == ORC_GUO) {
+        if (p->forcing == ORC_LI) {
+            /* Eq. 31: f^eq at v = u + F/(2 rho); Guo's source with v' in its
+             * second-order term. */
+            double vx = ux + Fx / (2.0 * rho), vy = uy + Fy / (2.0 * rho);
+            double c = p->sigma / ((tau - 0.5) * psi * psi);
+            orc_feq(rho, vx, vy, feq);
+            orc_guo_source(1.0 - 1.0 / (2.0 * tau), Fx, Fy, vx + c * Fx, vy + c * Fy, S);
+            for (int a = 0; a < 9; ++a) fstar[a] = f[a] - (f[a] - feq[a]) / tau + S[a];
+        } else if (p->forcing == ORC_GUO) {
             /* Eqs. 1, 2, 23: f^eq evaluated at v = u + F/(2 rho). */
             double vx = ux + Fx / (2.0 * rho), vy = uy + Fy / (2.0 * rho);
             orc_feq(rho, vx, vy, feq);
@@ -311,21 +329,21 @@ int orc_step(const orc_params *p, const double *f, double *fnext)
     int nx = p->nx, ny = p->ny, n = nx * ny;
     double *rho = malloc(sizeof(double) * n), *ux = malloc(sizeof(double) * n),
            *uy = malloc(sizeof(double) * n), *Fx = malloc(sizeof(double) * n),
-           *Fy = malloc(sizeof(double) * n);
-    int status = orc_macro(p, f, rho, ux, uy, NULL, Fx, Fy, NULL, NULL);
+           *Fy = malloc(sizeof(double) * n), *psi = malloc(sizeof(double) * n);
+    int status = orc_macro(p, f, rho, ux, uy, psi, Fx, Fy, NULL, NULL);
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             int i = y * nx + x;
             double fl[9], fs[9];
             for (int a = 0; a < 9; ++a) fl[a] = f[a * n + i];
-            orc_collide_node(p, fl, rho[i], ux[i], uy[i], Fx[i], Fy[i], fs);
+            orc_collide_node(p, fl, rho[i], ux[i], uy[i], Fx[i], Fy[i], psi[i], fs);
             for (int a = 0; a < 9; ++a) {
                 int xd = wrap(x + EX[a], nx), yd = wrap(y + EY[a], ny);
                 if (!isfinite(fs[a])) status = status ? status : ORC_E_NONFINITE;
                 fnext[a * n + yd * nx + xd] = fs[a];
             }
         }
-    free(rho); free(ux); free(uy); free(Fx); free(Fy);
+    free(rho); free(ux); free(uy); free(Fx); free(Fy); free(psi);
     return status;
 }
 

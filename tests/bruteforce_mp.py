@@ -95,6 +95,12 @@ def step(f, nx, ny, prm):
             elif prm["forcing"] == "guo":
                 fe, src = feq(r, v), guo(1 - 1 / (2 * tau), F, v)
                 fs = [fl[a] - (fl[a] - fe[a]) / tau + src[a] for a in range(9)]
+            elif prm["forcing"] == "li":
+                # Eq. 31: Guo's source with v' = v + sigma F / ((tau - 1/2) psi^2)
+                c = mpf(prm["sigma"]) / ((tau - mpf(1) / 2) * psi[(x, y)] ** 2)
+                vp = (v[0] + c * F[0], v[1] + c * F[1])
+                fe, src = feq(r, v), guo(1 - 1 / (2 * tau), F, vp)
+                fs = [fl[a] - (fl[a] - fe[a]) / tau + src[a] for a in range(9)]
             elif prm["forcing"] == "edm":
                 fe = feq(r, u)
                 fe2 = feq(r, (u[0] + F[0] / r, u[1] + F[1] / r))

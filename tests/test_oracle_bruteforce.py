@@ -4,7 +4,7 @@ import pytest
 
 from paper_1412_5170_gb300 import synth
 
-SCHEMES = [("bgk", "guo"), ("bgk", "edm"), ("bgk", "sc"), ("mrt", "guo")]
+SCHEMES = [("bgk", "guo"), ("bgk", "edm"), ("bgk", "sc"), ("mrt", "guo"), ("bgk", "li")]
 
 
 @pytest.mark.parametrize("nx,ny", [(4, 4), (5, 3)])
@@ -13,11 +13,12 @@ def test_oracle_matches_50_digit_stepper(orc, nx, ny, coll, forc):
     pytest.importorskip("mpmath")
     from mpmath import mpf
     from tests import bruteforce_mp as bf
-    prm = dict(T_over_Tc=0.75, K=0.5, tau=0.8, A=-0.3, collision=coll, forcing=forc,
-               s_e=0.8, s_eps=0.9, s_q=1.1)
+    li = forc == "li"   # Li et al.'s model: the Eq. 4 force (A = 0) and sigma of Eq. 31
+    prm = dict(T_over_Tc=0.75, K=0.5, tau=0.8, A=0.0 if li else -0.3, collision=coll, forcing=forc,
+               s_e=0.8, s_eps=0.9, s_q=1.1, sigma=0.105 if li else 0.0)
     f0 = synth.random_populations(nx, ny, seed=5, base=0.25, amp=0.2)
     p = orc.params(nx, ny, prm["T_over_Tc"], prm["tau"], prm["A"], prm["K"], coll, forc,
-                   s_e=0.8, s_eps=0.9, s_q=1.1)
+                   s_e=0.8, s_eps=0.9, s_q=1.1, sigma=prm["sigma"])
     steps = 6
     fo, st = orc.run(p, f0, steps)
     assert st == 0

@@ -13,7 +13,7 @@ GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_t
 SCHEMES = [("bgk", "guo"), ("bgk", "edm"), ("bgk", "sc"), ("mrt", "guo")]
 
 
-@pytest.mark.parametrize("coll,forc", SCHEMES)
+@pytest.mark.parametrize("coll,forc", SCHEMES + [("bgk", "li")])
 def test_global_mass_and_momentum_are_conserved(orc, coll, forc):
     """Collision conserves mass and adds F; sum_x F = 0 on a periodic lattice, and
     streaming only moves populations: total mass and momentum stay constant."""
@@ -21,7 +21,9 @@ def test_global_mass_and_momentum_are_conserved(orc, coll, forc):
     rg, rl, _ = cx.maxwell(0.85)
     nx, ny = 17, 15
     rho0 = synth.density_field(nx, ny, "droplet", rl, rg, 5.0, seed=3, noise_amp=1e-4)
-    p = orc.params(nx, ny, 0.85, 1.0, -0.304, 1.0, coll, forc, s_e=0.8, s_eps=0.8, s_q=1.1)
+    li = forc == "li"
+    p = orc.params(nx, ny, 0.85, 1.0, 0.0 if li else -0.304, 1.0, coll, forc, s_e=0.8, s_eps=0.8, s_q=1.1,
+                   sigma=0.105 if li else 0.0)
     f0 = orc.init_rest(rho0)
     f, st = orc.run(p, f0, 300)
     assert st == 0
@@ -79,11 +81,11 @@ def test_shear_wave_decays_at_the_lbgk_viscosity(orc, coll, tau):
     assert nu == pytest.approx((tau - 0.5) / 3.0, rel=0.01)
 
 
-def _slab(orc, tr, A, K, tau, forcing="guo", coll="bgk", steps=15000, nx=4, ny=64):
+def _slab(orc, tr, A, K, tau, forcing="guo", coll="bgk", steps=15000, nx=4, ny=64, sigma=0.0):
     from oracle import coexistence as cx
     rg, rl, _ = cx.maxwell(tr, K)
     rho0 = synth.density_field(nx, ny, "slab", rl, rg, ny / 4, seed=11)
-    p = orc.params(nx, ny, tr, tau, A, K, coll, forcing, s_e=0.8, s_eps=0.8, s_q=1.1)
+    p = orc.params(nx, ny, tr, tau, A, K, coll, forcing, s_e=0.8, s_eps=0.8, s_q=1.1, sigma=sigma)
     f, st = orc.run(p, orc.init_rest(rho0), steps)
     assert st == 0
     m, _ = orc.macro(p, f)
@@ -126,3 +128,50 @@ def test_table6_flat_interface_simulation(orc, K, A, key, rel):
     rl, rg = _slab(orc, 0.6, A, K, 1.5, "guo", steps=20000, ny=128)
     assert rg == pytest.approx(GOLD["table6"][key], rel=rel)
     assert rl == pytest.approx(0.406, abs=2e-3)
+
+
+# ---- Li et al.'s model (Sec. 4.3, Eqs. 31-32) ----
+
+def test_li_with_sigma_zero_is_guo_with_the_eq4_force(orc):
+    """Eq. 31 with sigma = 0 is Eq. 23, and Li et al.'s force (Eq. 4) is Eq. 6
+    with A = 0: one step of each from the same state is identical."""
+    nx, ny = 11, 9
+    f0 = synth.random_populations(nx, ny, seed=7, base=0.25, amp=0.2)
+    a, sa = orc.step(orc.params(nx, ny, 0.75, 0.9, 0.0, 0.5, "bgk", "li", sigma=0.0), f0)
+    b, sb = orc.step(orc.params(nx, ny, 0.75, 0.9, 0.0, 0.5, "bgk", "guo"), f0)
+    assert sa == sb == 0
+    np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("tr", [0.8, 0.7])
+def test_li_flat_interface_follows_the_eq32_mechanical_solution(orc, tr):
+    """Sec. 4.3.1 / Fig. 6: sigma = 0.105 sets eps = 16 sigma = 1.68 (Eq. 32
+    with alpha = 0, beta = 3, G = -1), and the flat-interface densities follow
+    the Eq. 18 solution for that eps; reading the paper's 'upsilon' as the
+    viscosity (tau - 1/2)/3 would triple the shift (eps ~ 5) and miss it by
+    far more."""
+    from oracle import coexistence as cx
+    mech_g, mech_l, _ = cx.mechanical(tr, 1.0, 1.68)
+    far_g, _, _ = cx.mechanical(tr, 1.0, 5.04)
+    rl, rg = _slab(orc, tr, 0.0, 1.0, 1.0, "li", sigma=0.105)
+    assert rg == pytest.approx(mech_g, rel=0.02)
+    assert rl == pytest.approx(mech_l, rel=2e-3)
+    assert abs(rg - mech_g) < 0.1 * abs(far_g - mech_g)
+
+
+def test_li_flat_interface_is_tau_independent(orc):
+    a = _slab(orc, 0.8, 0.0, 1.0, 0.8, "li", sigma=0.105)
+    b = _slab(orc, 0.8, 0.0, 1.0, 1.5, "li", sigma=0.105)
+    assert a[1] == pytest.approx(b[1], rel=1e-6)
+    assert a[0] == pytest.approx(b[0], rel=1e-7)
+
+
+def test_li_closer_to_mechanical_solution_than_kupershtokh_at_low_temperature(orc):
+    """Sec. 4.3.1 / Fig. 6: at T/Tc < 0.7-ish, with the same eps = 1.68, Li et
+    al.'s gas density is closer to the mechanical solution than the modified
+    Kupershtokh model's (A = -0.84)."""
+    from oracle import coexistence as cx
+    mech_g, _, _ = cx.mechanical(0.7, 1.0, 1.68)
+    li = _slab(orc, 0.7, 0.0, 1.0, 1.0, "li", sigma=0.105)
+    kup = _slab(orc, 0.7, -0.84, 1.0, 1.0, "guo")
+    assert abs(li[1] - mech_g) < 0.2 * abs(kup[1] - mech_g)

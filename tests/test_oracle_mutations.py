@@ -47,6 +47,11 @@ MUTATIONS = {
     "mrt_eps_row": ("M[2 * 9 + a] = 4.0 - 21.0 / 2.0 * e2", "M[2 * 9 + a] = 4.0 - 19.0 / 2.0 * e2"),
     "mrt_source_half": ("(1.0 - lam[k] / 2.0) * Sm[k]", "(1.0 - lam[k]) * Sm[k]"),
     "feq_u2_coefficient": ("- u2 / (2.0 * cs2));", "- u2 / cs2);"),
+    "li_shift_sign": ("vx + c * Fx, vy + c * Fy, S);", "vx - c * Fx, vy - c * Fy, S);"),
+    "li_psi_not_squared": ("double c = p->sigma / ((tau - 0.5) * psi * psi);",
+                           "double c = p->sigma / ((tau - 0.5) * psi);"),
+    "li_viscosity_denominator": ("double c = p->sigma / ((tau - 0.5) * psi * psi);",
+                                 "double c = p->sigma / ((tau - 0.5) / 3.0 * psi * psi);"),
 }
 
 
