@@ -56,7 +56,8 @@ extern "C" {
 #define LBM_E_UNSUPPORTED 8    /* valid request this build does not support */
 
 typedef enum { LBM_BGK = 0, LBM_MRT = 1 } lbm_collision;            /* Eq. 1 / Eq. 34 */
-typedef enum { LBM_GUO = 0, LBM_EDM = 1, LBM_SC = 2 } lbm_forcing;   /* Eq. 23 / Eq. 22 / Eq. 21 */
+/* Eq. 23 / Eq. 22 / Eq. 21 / Li et al.'s model, Eq. 31 (Sec. 4.3) */
+typedef enum { LBM_GUO = 0, LBM_EDM = 1, LBM_SC = 2, LBM_LI = 3 } lbm_forcing;
 typedef enum { LBM_FP64 = 0, LBM_FP32_DEV = 1 } lbm_precision;
 typedef enum { LBM_SLAB = 0, LBM_DROPLET = 1, LBM_BUBBLE = 2, LBM_DROPLET_ARRAY = 3 } lbm_preset;
 
@@ -73,7 +74,12 @@ typedef enum { LBM_SLAB = 0, LBM_DROPLET = 1, LBM_BUBBLE = 2, LBM_DROPLET_ARRAY 
  *                 LBM_FP32_DEV: populations stored in float as deviations
  *                 f_a - w_a rho_ref, arithmetic in float; reductions in double.
  *   rho_ref       reference density of LBM_FP32_DEV (use the vapour density);
- *                 ignored for LBM_FP64. */
+ *                 ignored for LBM_FP64.
+ *   sigma         LBM_LI only (Sec. 4.3, Eqs. 31-32): Guo's source with v
+ *                 replaced by v' = v + sigma F / ((tau - 1/2) psi^2) in its
+ *                 second-order term, which sets eps = 16 sigma for the Eq. 4
+ *                 force; LBM_LI requires BGK and A = 0 (Eq. 6 with A = 0 is
+ *                 Eq. 4) and sigma >= 0.  Must be 0 for the other forcings. */
 typedef struct {
     int32_t nx, ny;
     int32_t collision;   /* lbm_collision */
@@ -83,6 +89,7 @@ typedef struct {
     double T_over_Tc, tau, A, K;
     double s_e, s_eps, s_q;
     double rho_ref;
+    double sigma;
 } lbm_params;
 
 /* Whole-lattice observables at the current time t (FP64 reductions).
@@ -216,7 +223,7 @@ int lbm_autotune(lbm_ctx *ctx, int trial_steps, int *config, double *ms_per_step
  * synchronous; the batch owns its device memory and its CUDA stream. */
 typedef struct {
     int32_t collision;   /* lbm_collision */
-    int32_t forcing;     /* lbm_forcing (MRT: Guo only) */
+    int32_t forcing;     /* lbm_forcing (MRT: Guo only; not LBM_LI) */
     int32_t precision;   /* LBM_FP32_DEV */
     int32_t reserved;    /* 0 */
     double s_e, s_eps, s_q;   /* MRT rates shared by all instances */

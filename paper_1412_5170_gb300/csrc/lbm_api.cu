@@ -96,6 +96,7 @@ void launch_generic_scheme(lbm_ctx* c, const void* fin, void* fout)
     if (p.collision == LBM_MRT) launch_generic<T, C, MRT, GUO>(c, fin, fout);
     else if (p.forcing == LBM_GUO) launch_generic<T, C, BGK, GUO>(c, fin, fout);
     else if (p.forcing == LBM_EDM) launch_generic<T, C, BGK, EDM>(c, fin, fout);
+    else if (p.forcing == LBM_LI) launch_generic<T, C, BGK, LI>(c, fin, fout);
     else launch_generic<T, C, BGK, SC>(c, fin, fout);
 }
 

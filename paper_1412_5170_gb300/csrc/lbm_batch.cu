@@ -537,14 +537,33 @@ void drop_graphs(lbm_batch* b)
 
 // Work items: every running instance, 128-column strips, chunks of about
 // b->rows rows (never under 8).
+// Work items of the running instances: 128-column strips cut into row chunks
+// of about b->rows rows.  When the running instances hold too few strip rows
+// to give every SM about eight items at that length (the tail of a run, when
+// a few instances remain), the chunks shrink -- down to 16 rows -- so a step
+// is spread over more warps and its latency (one row walk) shortens.
 int build_items(lbm_batch* b, const int* host_state)
 {
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 1;
+    }
+    long long strip_rows = 0;
+    for (int i = 0; i < b->n; ++i) {
+        if (host_state && host_state[i] != B_RUNNING) continue;
+        const BInst& I = b->hinst[i];
+        strip_rows += (long long)((I.nx + 127) / 128) * I.ny;
+    }
+    const long long target = 8LL * nsm;
+    const int rows = (int)std::max<long long>(std::min<long long>(b->rows, strip_rows / target), std::min(16, b->rows));
     std::vector<BItem> it;
     for (int i = 0; i < b->n; ++i) {
         if (host_state && host_state[i] != B_RUNNING) continue;
         const BInst& I = b->hinst[i];
         const int nstrips = (I.nx + 127) / 128;
-        const int nch = std::max(1, (I.ny + b->rows / 2) / b->rows);
+        const int nch = std::max(1, (I.ny + rows / 2) / rows);
         for (int c = 0; c < nch; ++c) {
             const int y0 = int((long long)c * I.ny / nch), y1 = int((long long)(c + 1) * I.ny / nch);
             if (y1 <= y0) continue;
@@ -666,6 +685,7 @@ int lbm_batch_create(const lbm_batch_params* bp, const lbm_instance* inst, int n
     if (!bp || !inst || n < 1 || !out) return LBM_E_INVALID;
     *out = nullptr;
     if (bp->precision != LBM_FP32_DEV) return LBM_E_UNSUPPORTED;
+    if (bp->forcing == LBM_LI) return LBM_E_UNSUPPORTED;   // the batch carries no sigma
     lbm_batch* b = new (std::nothrow) lbm_batch();
     if (!b) return LBM_E_INVALID;
     b->n = n;

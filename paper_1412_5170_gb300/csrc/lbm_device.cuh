@@ -12,7 +12,7 @@
 namespace lbm {
 
 enum : int { BGK = 0, MRT = 1 };
-enum : int { GUO = 0, EDM = 1, SC = 2 };
+enum : int { GUO = 0, EDM = 1, SC = 2, LI = 3 };
 enum : unsigned { ST_NONFINITE = 1u, ST_EOS = 2u, ST_TIMEOUT = 4u, ST_ALIGN = 8u };
 
 // D2Q9 velocities (Sec. 2): 0 rest, 1-4 axes, 5-8 diagonals.
@@ -42,6 +42,7 @@ struct Coef {
     C guo_pre;    // 1 - 1/(2 tau)  (Eq. 23)
     C s_e, s_eps, s_q;  // MRT rates (Eq. 35); s_nu = omega
     C rho_ref;    // deviation reference (0 for FP64)
+    C li_c;       // sigma / (tau - 1/2): Li et al.'s v' = v + li_c F / psi^2 (Eq. 31)
     // MRT relaxation of moment m with rate s, equilibrium m^eq and source S,
     // already divided by the squared norm n of its row of M (M^-1 = M^T / n):
     //   (m - s (m - m^eq) + (1 - s/2) S) / n = r0 m + r1 m^eq + r2 S
@@ -108,10 +109,11 @@ __device__ __forceinline__ C feq_dev(int a, C drho, C rho, C ux, C uy, C usq15)
     return wt<C>(a) * (drho + rho * (C(3) * eu + C(4.5) * eu * eu - usq15));
 }
 
-// Collision of one node.  In: g (pulled deviations at time t), F.  Out: g
-// becomes the post-collision deviations; vx, vy receive v = u + F/(2 rho).
+// Collision of one node.  In: g (pulled deviations at time t), F, psi at the
+// node (used by Li et al.'s model only).  Out: g becomes the post-collision
+// deviations; vx, vy receive v = u + F/(2 rho).
 template <typename C, int COLL, int FORC>
-__device__ __forceinline__ void collide(C g[9], C Fx, C Fy, const Coef<C>& k, C& vx, C& vy, C& rho_out)
+__device__ __forceinline__ void collide(C g[9], C Fx, C Fy, const Coef<C>& k, C& vx, C& vy, C& rho_out, C psi)
 {
     C drho, jx, jy;
     moments(g, drho, jx, jy);
@@ -131,6 +133,21 @@ __device__ __forceinline__ void collide(C g[9], C Fx, C Fy, const Coef<C>& k, C&
             const C eF = C(ex(a)) * Fx + C(ey(a)) * Fy;
             const C ev = C(ex(a)) * vx + C(ey(a)) * vy;
             const C S = wt<C>(a) * k.guo_pre * (C(3) * eF + C(9) * ev * eF - vF3);
+            const C fe = feq_dev<C>(a, drho, rho, vx, vy, usq);
+            g[a] = g[a] + k.omega * (fe - g[a]) + S;
+        }
+    } else if constexpr (COLL == BGK && FORC == LI) {
+        // Eq. 31 (Li et al.): as Guo, with v' = v + sigma F / ((tau - 1/2) psi^2)
+        // in the second-order part of the source; F is Eq. 4's (A = 0).
+        const C c = cdiv(k.li_c, psi * psi);
+        const C wx = vx + c * Fx, wy = vy + c * Fy;
+        const C usq = C(1.5) * (vx * vx + vy * vy);
+        const C wF3 = C(3) * (wx * Fx + wy * Fy);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            const C eF = C(ex(a)) * Fx + C(ey(a)) * Fy;
+            const C ew = C(ex(a)) * wx + C(ey(a)) * wy;
+            const C S = wt<C>(a) * k.guo_pre * (C(3) * eF + C(9) * ew * eF - wF3);
             const C fe = feq_dev<C>(a, drho, rho, vx, vy, usq);
             g[a] = g[a] + k.omega * (fe - g[a]) + S;
         }

@@ -95,7 +95,15 @@ int lbm_validate_params(const lbm_params* p)
     if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return LBM_E_INVALID;
     if (!finite_pos(p->K) || !std::isfinite(p->A)) return LBM_E_INVALID;
     if (p->collision != LBM_BGK && p->collision != LBM_MRT) return LBM_E_INVALID;
-    if (p->forcing < LBM_GUO || p->forcing > LBM_SC) return LBM_E_INVALID;
+    if (p->forcing < LBM_GUO || p->forcing > LBM_LI) return LBM_E_INVALID;
+    if (!std::isfinite(p->sigma)) return LBM_E_INVALID;
+    if (p->forcing == LBM_LI) {
+        // Li et al.'s model: BGK collision, the Eq. 4 force (Eq. 6 with A = 0), sigma >= 0
+        if (p->collision != LBM_BGK) return LBM_E_UNSUPPORTED;
+        if (p->A != 0.0 || !(p->sigma >= 0.0)) return LBM_E_INVALID;
+    } else if (p->sigma != 0.0) {
+        return LBM_E_INVALID;
+    }
     if (p->precision != LBM_FP64 && p->precision != LBM_FP32_DEV) return LBM_E_INVALID;
     if (p->reserved != 0) return LBM_E_INVALID;
     if (p->collision == LBM_MRT) {

@@ -47,6 +47,7 @@ lbm::Coef<C> make_coef(const lbm_params& p)
     k.s_eps = C(p.s_eps);
     k.s_q = C(p.s_q);
     k.rho_ref = C(p.precision == LBM_FP64 ? 0.0 : p.rho_ref);
+    k.li_c = C(p.forcing == LBM_LI ? p.sigma / (p.tau - 0.5) : 0.0);
     const double rate[4] = {p.s_e, p.s_eps, p.s_q, 1.0 / p.tau};
     const double norm[4] = {36.0, 36.0, 12.0, 4.0};
     for (int i = 0; i < 4; ++i) {

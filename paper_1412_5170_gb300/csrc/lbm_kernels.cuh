@@ -95,7 +95,7 @@ k_step_generic(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, 
                      sp[c + W + 1], sp[c + W - 1], sp[c - W - 1], sp[c - W + 1]};
         C Fx, Fy, vx, vy, rho;
         force<C>(q, k, Fx, Fy);
-        collide<C, COLL, FORC>(g, Fx, Fy, k, vx, vy, rho);
+        collide<C, COLL, FORC>(g, Fx, Fy, k, vx, vy, rho, q.c);
         bad |= finite_bits<C>(g);
         const size_t o = (size_t)y * nx + x;
 #pragma unroll

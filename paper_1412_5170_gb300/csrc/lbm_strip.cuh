@@ -324,7 +324,7 @@ __device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restr
                     force<C>(q, k, Fx, Fy);
 #pragma unroll
                     for (int a = 0; a < 9; ++a) gj[a] = gc[a][j];
-                    collide<C, COLL, FORC>(gj, Fx, Fy, k, vx, vy, rho);
+                    collide<C, COLL, FORC>(gj, Fx, Fy, k, vx, vy, rho, q.c);
                     if (!isfinite(gj[0])) bad |= ST_NONFINITE;   // g0 closes on all others
 #pragma unroll
                     for (int a = 0; a < 9; ++a) o[a][j] = T(gj[a]);
@@ -418,6 +418,7 @@ int launch_strip_scheme(const lbm_params* p, const void* fin, void* fout, unsign
     if (p->collision == LBM_MRT) return launch_strip_cfg<T, C, MRT, GUO, NT, NS, CARRY>(p, fin, fout, status, s);
     if (p->forcing == LBM_GUO) return launch_strip_cfg<T, C, BGK, GUO, NT, NS, CARRY>(p, fin, fout, status, s);
     if (p->forcing == LBM_EDM) return launch_strip_cfg<T, C, BGK, EDM, NT, NS, CARRY>(p, fin, fout, status, s);
+    if (p->forcing == LBM_LI) return launch_strip_cfg<T, C, BGK, LI, NT, NS, CARRY>(p, fin, fout, status, s);
     return launch_strip_cfg<T, C, BGK, SC, NT, NS, CARRY>(p, fin, fout, status, s);
 }
 

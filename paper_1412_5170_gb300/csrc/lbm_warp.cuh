@@ -198,7 +198,7 @@ __device__ __forceinline__ bool warp_walk(const float* __restrict__ fin, float* 
                 force<C>(q, k, Fx, Fy);
 #pragma unroll
                 for (int a = 0; a < 9; ++a) gj[a] = gc[a][j];
-                collide<C, COLL, FORC>(gj, Fx, Fy, k, vx, vy, rho);
+                collide<C, COLL, FORC>(gj, Fx, Fy, k, vx, vy, rho, q.c);
                 if (!isfinite(gj[0])) mybad |= ST_NONFINITE;   // g0 closes on all others
 #pragma unroll
                 for (int a = 0; a < 9; ++a) o[a][j] = float(gj[a]);
@@ -301,6 +301,7 @@ int launch_warp_scheme(const lbm_params* p, const void* fin, void* fout, unsigne
     if (p->collision == LBM_MRT) return launch_warp_cfg<float, MRT, GUO, NS, CARRY>(p, fin, fout, status, s);
     if (p->forcing == LBM_GUO) return launch_warp_cfg<float, BGK, GUO, NS, CARRY>(p, fin, fout, status, s);
     if (p->forcing == LBM_EDM) return launch_warp_cfg<float, BGK, EDM, NS, CARRY>(p, fin, fout, status, s);
+    if (p->forcing == LBM_LI) return launch_warp_cfg<float, BGK, LI, NS, CARRY>(p, fin, fout, status, s);
     return launch_warp_cfg<float, BGK, SC, NS, CARRY>(p, fin, fout, status, s);
 }
 

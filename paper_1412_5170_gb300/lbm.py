@@ -22,11 +22,11 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 OK, E_INVALID, E_CUDA, E_NONFINITE, E_EOS_DOMAIN, E_TIMEOUT, E_NOT_CONVERGED, E_IO, E_UNSUPPORTED = range(9)
 BGK, MRT = 0, 1
-GUO, EDM, SC = 0, 1, 2
+GUO, EDM, SC, LI = 0, 1, 2, 3
 FP64, FP32_DEV = 0, 1
 SLAB, DROPLET, BUBBLE, DROPLET_ARRAY = 0, 1, 2, 3
 COLLISION = {"bgk": BGK, "mrt": MRT}
-FORCING = {"guo": GUO, "edm": EDM, "sc": SC}
+FORCING = {"guo": GUO, "edm": EDM, "sc": SC, "li": LI}
 PRECISION = {"fp64": FP64, "fp32": FP32_DEV}
 PRESET = {"slab": SLAB, "droplet": DROPLET, "bubble": BUBBLE, "droplet_array": DROPLET_ARRAY}
 
@@ -36,7 +36,7 @@ class lbm_params(ctypes.Structure):
                 ("forcing", ctypes.c_int32), ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("T_over_Tc", ctypes.c_double), ("tau", ctypes.c_double), ("A", ctypes.c_double),
                 ("K", ctypes.c_double), ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double),
-                ("s_q", ctypes.c_double), ("rho_ref", ctypes.c_double)]
+                ("s_q", ctypes.c_double), ("rho_ref", ctypes.c_double), ("sigma", ctypes.c_double)]
 
 
 class lbm_stats_t(ctypes.Structure):
@@ -167,12 +167,12 @@ def maxwell(T_over_Tc: float):
 
 
 def make_params(nx, ny, T_over_Tc, tau, A, K=1.0, collision="bgk", forcing="guo", precision="fp64",
-                s_e=1.0, s_eps=1.0, s_q=1.0, rho_ref=None) -> lbm_params:
+                s_e=1.0, s_eps=1.0, s_q=1.0, rho_ref=None, sigma=0.0) -> lbm_params:
     if rho_ref is None:
         rho_ref = maxwell(T_over_Tc)[0] if precision == "fp32" else 0.0
     return lbm_params(int(nx), int(ny), COLLISION[collision], FORCING[forcing], PRECISION[precision], 0,
                       float(T_over_Tc), float(tau), float(A), float(K), float(s_e), float(s_eps), float(s_q),
-                      float(rho_ref))
+                      float(rho_ref), float(sigma))
 
 
 def _host_ptr(a: np.ndarray):

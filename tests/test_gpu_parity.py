@@ -19,7 +19,7 @@ from paper_1412_5170_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-SCHEMES = [("bgk", "guo"), ("bgk", "edm"), ("bgk", "sc"), ("mrt", "guo")]
+SCHEMES = [("bgk", "guo"), ("bgk", "edm"), ("bgk", "sc"), ("mrt", "guo"), ("bgk", "li")]
 MRT = dict(s_e=0.8, s_eps=0.8, s_q=1.1)
 
 
@@ -28,7 +28,10 @@ def run_pair(lbm, nx, ny, steps, coll, forc, tr=0.8, tau=0.9, A=-0.304, K=1.0, p
     rv, rl = lbm.maxwell(tr)
     size = size if size is not None else max(2.0, min(nx, ny) / 4)
     rho0 = synth.density_field(nx, ny, kind, rl, rv, size, seed=seed)
-    p = lbm.make_params(nx, ny, tr, tau, A, K, coll, forc, precision, **MRT)
+    sigma = 0.0
+    if forc == "li":   # Li et al.'s model: the Eq. 4 force (A = 0) and the paper's sigma
+        A, sigma = 0.0, 0.105
+    p = lbm.make_params(nx, ny, tr, tau, A, K, coll, forc, precision, sigma=sigma, **MRT)
     with lbm.Lattice(p) as lat:
         if variant is not None:
             lat.variant = variant
@@ -36,7 +39,7 @@ def run_pair(lbm, nx, ny, steps, coll, forc, tr=0.8, tau=0.9, A=-0.304, K=1.0, p
         lat.step(steps)
         f_gpu = lat.read_populations()
         st = lat.stats()
-    q = oracle.params(nx, ny, tr, tau, A, K, coll, forc, **MRT)
+    q = oracle.params(nx, ny, tr, tau, A, K, coll, forc, sigma=sigma, **MRT)
     f_ref, ost = oracle.run(q, oracle.init_rest(rho0), steps)
     return f_gpu, f_ref, st, ost
 
