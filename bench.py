@@ -456,6 +456,129 @@ def run_warmstart(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args):
+    """The static-droplet parameter sweep (256x256, R = 40, noise 1e-6): T/Tc
+    in {0.5 .. 0.9} x tau in {0.6, 0.8, 1.0} x {BGK, MRT} x K in {1, 1/4, 1/16},
+    each run for --sweep-steps steps in FP64 and in FP32 deviations on the
+    single-lattice path; reports the coexistence densities (centre / corner
+    node), density ratio and Us_max of every run and the FP32 error against
+    FP64 (bars: densities 1e-4 relative, Us_max 5 %)."""
+    import numpy as np
+    import torch
+
+    from paper_1412_5170_gb300 import lbm
+
+    torch.cuda.set_device(0)
+    A = args.sweep_A
+    rows = []
+    t0 = time.perf_counter()
+    idx = 0
+    for coll in ("bgk", "mrt"):
+        for T in (0.5, 0.6, 0.7, 0.8, 0.9):
+            for tau in (0.6, 0.8, 1.0):
+                for K in (1.0, 0.25, 0.0625):
+                    seed = 20141217 + 1000 + idx
+                    idx += 1
+                    res = {}
+                    for prec in ("fp64", "fp32"):
+                        p = lbm.make_params(256, 256, T, tau, A, K, coll, "guo", prec, **MRT)
+                        with lbm.Lattice(p) as lat:
+                            lat.init_preset("droplet", 40.0, seed=seed)
+                            lat.autotune(3)
+                            ts = time.perf_counter()
+                            lat.step(args.sweep_steps)
+                            st = lat.stats()
+                            res[prec] = dict(status=st["status"], rho_l=st["rho_center"], rho_v=st["rho_corner"],
+                                             us=st["max_v"], s=time.perf_counter() - ts)
+                    a, b = res["fp64"], res["fp32"]
+                    ok = a["status"] == 0 and b["status"] == 0 and np.isfinite(a["rho_l"]) and a["rho_l"] > 1.5 * a["rho_v"]
+                    row = dict(coll=coll, T=T, tau=tau, K=K, status=[a["status"], b["status"]],
+                               fp64=[a["rho_l"], a["rho_v"], a["us"]], fp32=[b["rho_l"], b["rho_v"], b["us"]],
+                               two_phase=bool(ok))
+                    if ok:
+                        row["ratio"] = a["rho_l"] / a["rho_v"]
+                        row["err"] = [abs(b["rho_l"] / a["rho_l"] - 1), abs(b["rho_v"] / a["rho_v"] - 1),
+                                      abs(b["us"] / a["us"] - 1)]
+                    rows.append(row)
+                    print("  %s T %.1f tau %.1f K %.4f  fp64 %s  fp32 %s  %s" % (
+                        coll, T, tau, K, [round(v, 7) for v in row["fp64"]], [round(v, 7) for v in row["fp32"]],
+                        row.get("err")), file=sys.stderr, flush=True)
+    good = [r for r in rows if r["two_phase"]]
+    err = np.array([r["err"] for r in good]) if good else np.zeros((0, 3))
+    line = {
+        "metric": "FP32-deviation vs FP64 coexistence and Us_max, static-droplet sweep", "unit": "relative error",
+        "runs": len(rows), "two_phase_stable": len(good),
+        "failed_fp64": sum(1 for r in rows if r["status"][0] != 0), "failed_fp32": sum(1 for r in rows if r["status"][1] != 0),
+        "max_err": {"rho_l": float(err[:, 0].max()) if len(err) else None,
+                    "rho_v": float(err[:, 1].max()) if len(err) else None,
+                    "us_max": float(err[:, 2].max()) if len(err) else None},
+        "within_bars": int(np.sum((err[:, 0] < 1e-4) & (err[:, 1] < 1e-4) & (err[:, 2] < 0.05))) if len(err) else 0,
+        "max_density_ratio": max((r["ratio"] for r in good), default=None),
+        "rows": rows, "wall_s": time.perf_counter() - t0,
+        "config": {"workload": "static droplet 256x256, R = 40, noise 1e-6, %d steps, MRT rates 0.8/0.8/1.1, "
+                               "Guo forcing, A = %g" % (args.sweep_steps, A)},
+    }
+    print(json.dumps(line), flush=True)
+
+
+COEX_SCHEMES = [
+    # label, collision, forcing, A, K, sigma, eps of the mechanical solution
+    ("guo eps0.52", "bgk", "guo", -0.26, 1.0, 0.0, 0.52),
+    ("edm eps0.52", "bgk", "edm", -0.26, 1.0, 0.0, 0.52),
+    ("sc eps0.52", "bgk", "sc", -0.26, 1.0, 0.0, 0.52),
+    ("guo eps1.68", "bgk", "guo", -0.84, 1.0, 0.0, 1.68),
+    ("li sigma0.105", "bgk", "li", 0.0, 1.0, 0.105, 1.68),
+    ("mrt guo eps1.68", "mrt", "guo", -0.84, 1.0, 0.0, 1.68),
+    ("guo K0.1 eps2", "bgk", "guo", -1.0, 0.1, 0.0, 2.0),
+]
+
+
+def coexistence_curve(lbm, coll, forc, A, K, sigma, T, steps, tau=1.0, ny=128, nx=8):
+    """Flat-interface coexistence densities (mid row, edge row) of one FP64 slab run."""
+    rv, rl = lbm.maxwell(T)
+    p = lbm.make_params(nx, ny, T, tau, A, K, coll, forc, "fp64", sigma=sigma, **MRT)
+    with lbm.Lattice(p) as lat:
+        lat.init_preset("slab", ny / 4, rho_l=rl, rho_v=rv, seed=11)
+        lat.autotune(3)
+        lat.step(steps)
+        st = lat.stats()
+    return st["status"], st["rho_row_mid"], st["rho_row0"]
+
+
+def _solution(fn, *a):
+    """A host coexistence solver's (rho_v, rho_l), or (None, None) where it has no root."""
+    try:
+        return fn(*a)
+    except Exception:
+        return None, None
+
+
+def run_coexistence(args):
+    """Coexistence curves of flat interfaces (the data behind Figs. 2-6 and
+    Table 6) for the paper's schemes against the Maxwell construction
+    (Eq. 19) and the mechanical-stability solution (Eq. 18) of the same eps,
+    both from liblbm's host solvers."""
+    from paper_1412_5170_gb300 import lbm
+
+    t0 = time.perf_counter()
+    temps = [0.5, 0.55, 0.6, 0.65, 0.7, 0.75, 0.8, 0.85, 0.9, 0.95]
+    rows = []
+    for label, coll, forc, A, K, sigma, eps in COEX_SCHEMES:
+        for T in temps:
+            st, rl, rg = coexistence_curve(lbm, coll, forc, A, K, sigma, T, args.coex_steps)
+            mg, ml = _solution(lbm.mechanical, T, K, eps)
+            xg, xl = lbm.maxwell(T)
+            rows.append(dict(scheme=label, T=T, status=st, rho_l=rl, rho_g=rg, mech=[ml, mg], maxwell=[xl, xg],
+                             rel_mech=[rl / ml - 1, rg / mg - 1] if st == 0 and mg else None,
+                             rel_maxwell=[rl / xl - 1, rg / xg - 1] if st == 0 else None))
+            print("  %-16s T %.2f status %d rho_l %.6f rho_g %.6g  mech %s %s  maxwell %.6f %.6g" % (
+                label, T, st, rl, rg, ml, mg, xl, xg), file=sys.stderr, flush=True)
+    line = {"metric": "flat-interface coexistence densities vs Eqs. 18-19", "unit": "relative deviation",
+            "rows": rows, "steps": args.coex_steps, "wall_s": time.perf_counter() - t0,
+            "config": {"workload": "slab 8x128 (half-width 32), FP64, tau = 1, MRT rates 0.8/0.8/1.1"}}
+    print(json.dumps(line), flush=True)
+
+
 def fp64_run_to_steady(lat, kind, tol, every, max_steps):
     """Cold single-lattice run until both coexistence densities (centre and
     corner, or mid and edge row for a slab) change by less than tol relative
@@ -483,7 +606,10 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="throughput", choices=["throughput", "warmstart"])
+    ap.add_argument("--mode", default="throughput", choices=["throughput", "warmstart", "sweep", "coexistence"])
+    ap.add_argument("--coex-steps", type=int, default=40000)
+    ap.add_argument("--sweep-steps", type=int, default=30000)
+    ap.add_argument("--sweep-A", type=float, default=-0.84)
     ap.add_argument("--ws-train", type=int, default=2000)
     ap.add_argument("--ws-test", type=int, default=256)
     ap.add_argument("--ws-epochs", type=int, default=3000)
@@ -509,6 +635,10 @@ def main():
         run_reference(args)
     elif args.mode == "warmstart":
         run_warmstart(args)
+    elif args.mode == "sweep":
+        run_sweep(args)
+    elif args.mode == "coexistence":
+        run_coexistence(args)
     else:
         run_ours(args)
 

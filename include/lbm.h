@@ -124,6 +124,15 @@ double lbm_tc(void);
  * vapour and liquid densities; LBM_E_INVALID if T/Tc is outside (0, 1). */
 int lbm_maxwell(double T_over_Tc, double *rho_v, double *rho_l);
 
+/* Mechanical-stability coexistence densities (Sec. 3.1, Eq. 18) of the
+ * Eq. 29/30 EOS scaled by K, with psi^2 = 2 (rho/3 - p0) (Eq. 7, G = -1) and
+ * exponent eps (eps = -2A for Eq. 6's force, 16 sigma for Li et al.'s model,
+ * Eq. 32): p0(rho_v) = p0(rho_l) = p_c and the integral of (p_c - p0)
+ * psi'/psi^(1+eps) from rho_v to rho_l vanishes.  Host FP64 (bisection on p_c,
+ * Gauss-Legendre quadrature in log rho).  LBM_E_INVALID if T/Tc is outside
+ * (0, 1), K <= 0, or no root is bracketed. */
+int lbm_mechanical(double T_over_Tc, double K, double eps, double *rho_v, double *rho_l);
+
 /* ---- single-lattice context ---- */
 
 /* Device bytes a context needs for p (populations x2, moment and snapshot

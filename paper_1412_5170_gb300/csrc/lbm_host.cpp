@@ -49,6 +49,93 @@ extern "C" double lbm_tc(void)
     return (0.18727 / 0.4963) * 1.0 / (4.0 * 1.0);
 }
 
+namespace {
+
+// Spinodal densities s1 < s2 of the CS isotherm at temperature T (dp/drho
+// changes sign + -> - at s1 and - -> + at s2); false if there are none.
+bool spinodals(double T, double& s1, double& s2)
+{
+    const int N = 20000;
+    double prev = cs_dp(1e-6, T), rprev = 1e-6;
+    s1 = s2 = -1;
+    for (int i = 1; i <= N && s2 < 0; ++i) {
+        const double r = 1e-6 + (0.95 - 1e-6) * i / N;
+        const double d = cs_dp(r, T);
+        if (s1 < 0 && prev > 0 && d <= 0) s1 = bisect([&](double x) { return cs_dp(x, T); }, rprev, r);
+        else if (s1 > 0 && prev < 0 && d >= 0) s2 = bisect([&](double x) { return cs_dp(x, T); }, rprev, r);
+        prev = d;
+        rprev = r;
+    }
+    return s1 > 0 && s2 > 0;
+}
+
+// Gas and liquid densities at which the CS isotherm (scaled by K, which moves
+// no root) reaches the pressure K * pc_unit.
+void branches(double T, double s1, double s2, double pc_unit, double& rg, double& rl)
+{
+    const double lg = bisect([&](double l) { return cs_p(std::exp(l), T) - pc_unit; }, std::log(1e-30), std::log(s1));
+    rg = std::exp(lg);
+    rl = bisect([&](double r) { return cs_p(r, T) - pc_unit; }, s2, 1.0 - 1e-12);
+}
+
+// 8-point Gauss-Legendre nodes and weights on [-1, 1].
+const double kGLx[8] = {-0.9602898564975363, -0.7966664774136267, -0.5255324099163290, -0.1834346424956498,
+                        0.1834346424956498,  0.5255324099163290,  0.7966664774136267,  0.9602898564975363};
+const double kGLw[8] = {0.1012285362903763, 0.2223810344533745, 0.3137066458778873, 0.3626837833783620,
+                        0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
+
+// int_a^b g(rho) d rho over n intervals uniform in log rho (composite 8-point
+// Gauss-Legendre in l = ln rho, d rho = rho dl).
+template <typename G>
+double integrate_log(G g, double a, double b, int n = 400)
+{
+    const double la = std::log(a), h = (std::log(b) - la) / n;
+    double sum = 0;
+    for (int i = 0; i < n; ++i) {
+        const double c = la + (i + 0.5) * h;
+        for (int j = 0; j < 8; ++j) {
+            const double r = std::exp(c + 0.5 * h * kGLx[j]);
+            sum += kGLw[j] * g(r) * r;
+        }
+    }
+    return 0.5 * h * sum;
+}
+
+}  // namespace
+
+extern "C" int lbm_mechanical(double T_over_Tc, double K, double eps, double* rho_v, double* rho_l)
+{
+    if (!rho_v || !rho_l || !(T_over_Tc > 0.05 && T_over_Tc < 1.0) || !finite_pos(K) || !std::isfinite(eps))
+        return LBM_E_INVALID;
+    const double T = T_over_Tc * lbm_tc();
+    double s1, s2;
+    if (!spinodals(T, s1, s2)) return LBM_E_INVALID;
+    // Eq. 18 with p0 = K p_CS (Eq. 30) and, from Eq. 7 with G = -1,
+    // psi^2 = 2 (rho/3 - p0), so psi' / psi^(1+eps) = (1/3 - p0') / psi^(2+eps).
+    auto mech = [&](double pc_unit) {
+        double rg, rl;
+        branches(T, s1, s2, pc_unit, rg, rl);
+        const double pc = K * pc_unit;
+        return integrate_log([&](double r) {
+            const double p0 = K * cs_p(r, T);
+            const double psi2 = 2.0 * (r / 3.0 - p0);
+            return (pc - p0) * (1.0 / 3.0 - K * cs_dp(r, T)) / std::pow(psi2, 1.0 + 0.5 * eps);
+        }, rg, rl);
+    };
+    const double p_hi = cs_p(s1, T);
+    const double p_lo = std::fmax(cs_p(s2, T), 0.0);
+    const double lo = p_lo > 0 ? p_lo * (1 + 1e-12) : p_hi * 1e-14;
+    const double hi = p_hi * (1 - 1e-14);
+    const double flo = mech(lo), fhi = mech(hi);
+    if (!std::isfinite(flo) || !std::isfinite(fhi) || (flo < 0) == (fhi < 0)) return LBM_E_INVALID;
+    const double pc = bisect(mech, lo, hi, 120);
+    double rg, rl;
+    branches(T, s1, s2, pc, rg, rl);
+    *rho_v = rg;
+    *rho_l = rl;
+    return LBM_OK;
+}
+
 extern "C" int lbm_maxwell(double T_over_Tc, double* rho_v, double* rho_l)
 {
     if (!rho_v || !rho_l || !(T_over_Tc > 0.05 && T_over_Tc < 1.0)) return LBM_E_INVALID;

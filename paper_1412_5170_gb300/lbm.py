@@ -85,6 +85,7 @@ _PROTOS = {
     "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "lbm_version": (ctypes.c_int, []),
     "lbm_tc": (ctypes.c_double, []),
+    "lbm_mechanical": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _dp]),
     "lbm_maxwell": (ctypes.c_int, [ctypes.c_double, _dp, _dp]),
     "lbm_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(lbm_params), ctypes.POINTER(ctypes.c_size_t)]),
     "lbm_create": (ctypes.c_int, [ctypes.POINTER(lbm_params), _vp, _vp, ctypes.c_size_t, ctypes.POINTER(_vp)]),
@@ -163,6 +164,13 @@ def maxwell(T_over_Tc: float):
     """(rho_v, rho_l) of the Maxwell construction (Eq. 19), host FP64."""
     rv, rl = ctypes.c_double(), ctypes.c_double()
     check(lbm_maxwell(float(T_over_Tc), ctypes.byref(rv), ctypes.byref(rl)), "lbm_maxwell")
+    return rv.value, rl.value
+
+
+def mechanical(T_over_Tc: float, K: float, eps: float):
+    """(rho_v, rho_l) of the mechanical-stability condition (Eq. 18)."""
+    rv, rl = ctypes.c_double(), ctypes.c_double()
+    check(lbm_mechanical(float(T_over_Tc), float(K), float(eps), ctypes.byref(rv), ctypes.byref(rl)), "lbm_mechanical")
     return rv.value, rl.value
 
 

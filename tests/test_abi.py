@@ -65,3 +65,16 @@ def test_invalid_parameters_are_rejected(lbm):
     p = lbm.make_params(16, 16, 0.7, 0.8, -0.3, collision="mrt", s_e=2.5)
     assert lbm.lbm_workspace_bytes(ctypes.byref(p), ctypes.byref(n)) == lbm.E_INVALID
     assert lbm.lbm_maxwell(1.2, None, None) == lbm.E_INVALID
+
+
+@pytest.mark.parametrize("tr,K,eps", [(0.8, 1.0, 0.52), (0.6, 1.0, 1.68), (0.6, 0.1, 2.0), (0.7, 0.5, 1.68),
+                                      (0.9, 1.0, 1.0), (0.55, 0.25, 1.68)])
+def test_library_mechanical_solution_matches_oracle(lbm, orc, tr, K, eps):
+    """The library's Eq. 18 solver (bisection + Gauss-Legendre in log rho)
+    against the oracle's (scipy brentq + adaptive quad, finite-difference
+    psi'): independent codes, same densities."""
+    from oracle import coexistence as cx
+    rv, rl = lbm.mechanical(tr, K, eps)
+    g, l, _ = cx.mechanical(tr, K, eps)
+    assert rv == pytest.approx(g, rel=1e-6)
+    assert rl == pytest.approx(l, rel=1e-8)
