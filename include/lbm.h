@@ -199,8 +199,11 @@ int lbm_save(lbm_ctx *ctx, const char *path);
 int lbm_load(lbm_ctx *ctx, const char *path);
 
 /* Kernel variant in use: 0 = generic tiled kernel (any nx), 1 = pipelined
- * strip kernel (nx % 4 == 0).  lbm_set_variant forces one (LBM_E_UNSUPPORTED
- * if the lattice does not allow it); -1 restores the automatic choice. */
+ * strip kernel (nx % 4 == 0).  lbm_set_variant forces one (1 selects the
+ * first strip configuration; LBM_E_UNSUPPORTED if the lattice does not
+ * allow it); -1 restores the automatic choice: the strip kernel where it
+ * applies (for FP32 lattices at least 1024 wide its 256-thread, two-stage
+ * configuration), else the generic kernel.  lbm_autotune picks by timing. */
 int lbm_get_variant(lbm_ctx *ctx, int *variant);
 int lbm_set_variant(lbm_ctx *ctx, int variant);
 

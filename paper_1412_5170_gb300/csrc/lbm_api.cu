@@ -100,7 +100,22 @@ void launch_generic_scheme(lbm_ctx* c, const void* fin, void* fout)
     else launch_generic<T, C, BGK, SC>(c, fin, fout);
 }
 
-int default_config(const lbm_params& p) { return lbm_strip_supported(&p) ? 1 : 0; }
+// Without autotuning: the strip kernel where it applies -- for FP32 lattices
+// at least 1024 wide the 256-thread, two-stage carried configuration (the
+// fastest measured on large lattices), otherwise the first strip
+// configuration -- else the generic kernel.
+int default_config(const lbm_params& p)
+{
+    if (!lbm_strip_supported(&p)) return 0;
+    if (p.precision == LBM_FP32_DEV && p.nx >= 1024) {
+        const int n = lbm_strip_config_count(p.precision);
+        for (int i = 0; i < n; ++i) {
+            const StripConfig sc = lbm_strip_config(p.precision, i);
+            if (sc.threads == 256 && sc.stages == 2) return i + 1;
+        }
+    }
+    return 1;
+}
 
 int n_configs(const lbm_params& p) { return 1 + (lbm_strip_supported(&p) ? lbm_strip_config_count(p.precision) : 0); }
 

@@ -356,9 +356,10 @@ __device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restr
     return true;
 }
 
-// One lattice, grid (strips, row chunks).
-template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY>
-__global__ void __launch_bounds__(NT)
+// One lattice, grid (strips, row chunks).  MINB > 1 asks the compiler to fit
+// MINB CTAs per SM in the register file (at the price of spills if needed).
+template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
 k_step_strip(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, int nchunks, Coef<C> k,
              unsigned* __restrict__ status)
 {
@@ -388,11 +389,11 @@ constexpr size_t strip_smem()
 // One launch over the whole lattice: strips of 4*NT columns, and as many row
 // chunks as fill every resident CTA slot once (one wave), but no chunk shorter
 // than 16 rows, so the two halo rows per chunk stay a small overhead.
-template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY>
+template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY, int MINB>
 int launch_strip_cfg(const lbm_params* p, const void* fin, void* fout, unsigned* status, cudaStream_t s)
 {
     constexpr size_t smem = strip_smem<T, C, NT, NS>();
-    auto kern = k_step_strip<T, C, COLL, FORC, NT, NS, CARRY>;
+    auto kern = k_step_strip<T, C, COLL, FORC, NT, NS, CARRY, MINB>;
     static int per_sm = 0, nsm = 0;    // per instantiation (one device per process)
     if (per_sm == 0) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -412,14 +413,14 @@ int launch_strip_cfg(const lbm_params* p, const void* fin, void* fout, unsigned*
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_E_CUDA;
 }
 
-template <typename T, typename C, int NT, int NS, bool CARRY = false>
+template <typename T, typename C, int NT, int NS, bool CARRY = false, int MINB = 1>
 int launch_strip_scheme(const lbm_params* p, const void* fin, void* fout, unsigned* status, cudaStream_t s)
 {
-    if (p->collision == LBM_MRT) return launch_strip_cfg<T, C, MRT, GUO, NT, NS, CARRY>(p, fin, fout, status, s);
-    if (p->forcing == LBM_GUO) return launch_strip_cfg<T, C, BGK, GUO, NT, NS, CARRY>(p, fin, fout, status, s);
-    if (p->forcing == LBM_EDM) return launch_strip_cfg<T, C, BGK, EDM, NT, NS, CARRY>(p, fin, fout, status, s);
-    if (p->forcing == LBM_LI) return launch_strip_cfg<T, C, BGK, LI, NT, NS, CARRY>(p, fin, fout, status, s);
-    return launch_strip_cfg<T, C, BGK, SC, NT, NS, CARRY>(p, fin, fout, status, s);
+    if (p->collision == LBM_MRT) return launch_strip_cfg<T, C, MRT, GUO, NT, NS, CARRY, MINB>(p, fin, fout, status, s);
+    if (p->forcing == LBM_GUO) return launch_strip_cfg<T, C, BGK, GUO, NT, NS, CARRY, MINB>(p, fin, fout, status, s);
+    if (p->forcing == LBM_EDM) return launch_strip_cfg<T, C, BGK, EDM, NT, NS, CARRY, MINB>(p, fin, fout, status, s);
+    if (p->forcing == LBM_LI) return launch_strip_cfg<T, C, BGK, LI, NT, NS, CARRY, MINB>(p, fin, fout, status, s);
+    return launch_strip_cfg<T, C, BGK, SC, NT, NS, CARRY, MINB>(p, fin, fout, status, s);
 }
 
 }  // namespace lbm

@@ -7,21 +7,28 @@ using namespace lbm;
 
 // {threads, stages, kind}: kind 1 / 2 select the warp-per-strip kernel
 // (lbm_warp.cuh) re-reading rows from shared memory / keeping them in
-// registers; kind 0 / 3 the block-strip kernel (lbm_strip.cuh) likewise.
+// registers; kind 0 / 3 the block-strip kernel (lbm_strip.cuh) likewise;
+// kind 4 the register-carrying block strip held to 128 registers so that
+// 16 warps share an SM (4 CTAs of 128 threads or 2 of 256).
 extern const StripConfig kStripF32[] = {{128, 3, 3}, {64, 3, 3}, {64, 4, 3}, {128, 4, 3},
-                                        {32, 3, 1}, {32, 4, 1}, {128, 3, 0}};
+                                        {32, 3, 1}, {32, 4, 1}, {128, 3, 0}, {128, 2, 4}, {256, 2, 4}, {512, 2, 4}};
 extern const int kStripF32Count = sizeof(kStripF32) / sizeof(kStripF32[0]);
 
 int lbm_strip_launch_f32(const lbm_params* p, int cfg, const void* fin, void* fout, unsigned* st, cudaStream_t s)
 {
     switch (cfg) {
-    case 0: return launch_strip_scheme<float, float, 128, 3, true>(p, fin, fout, st, s);
-    case 1: return launch_strip_scheme<float, float, 64, 3, true>(p, fin, fout, st, s);
-    case 2: return launch_strip_scheme<float, float, 64, 4, true>(p, fin, fout, st, s);
-    case 3: return launch_strip_scheme<float, float, 128, 4, true>(p, fin, fout, st, s);
+    // The last template argument is the CTAs per SM the shared memory of the
+    // configuration allows; the register budget is held to match it.
+    case 0: return launch_strip_scheme<float, float, 128, 3, true, 3>(p, fin, fout, st, s);
+    case 1: return launch_strip_scheme<float, float, 64, 3, true, 6>(p, fin, fout, st, s);
+    case 2: return launch_strip_scheme<float, float, 64, 4, true, 5>(p, fin, fout, st, s);
+    case 3: return launch_strip_scheme<float, float, 128, 4, true, 2>(p, fin, fout, st, s);
     case 4: return launch_warp_scheme<3, false>(p, fin, fout, st, s);
     case 5: return launch_warp_scheme<4, false>(p, fin, fout, st, s);
-    case 6: return launch_strip_scheme<float, float, 128, 3, false>(p, fin, fout, st, s);
+    case 6: return launch_strip_scheme<float, float, 128, 3, false, 3>(p, fin, fout, st, s);
+    case 7: return launch_strip_scheme<float, float, 128, 2, true, 4>(p, fin, fout, st, s);
+    case 8: return launch_strip_scheme<float, float, 256, 2, true, 2>(p, fin, fout, st, s);
+    case 9: return launch_strip_scheme<float, float, 512, 2, true, 1>(p, fin, fout, st, s);
     default: return LBM_E_INVALID;
     }
 }
