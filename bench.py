@@ -474,7 +474,7 @@ def run_batch(args):
     with lbm.Batch(inst, collision="mrt") as b:
         nodes = b.nodes
         b.init()
-        ns, rows, ms_tune = b.autotune(5)
+        ns, rows, carry, ms_tune = b.autotune(5)
         b.step(args.warmup)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -497,7 +497,7 @@ def run_batch(args):
         "roofline": {"bound": "hbm", "achieved": 72.0 * nodes / t_step / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": 72.0 * nodes / t_step / 1e9 / peak, "peak_kind": "%s (hbm_gbs, copy)" % peak_kind,
                      "kernel": "k_step_batch (every instance running, host-timed over %d steps)" % args.batch_steps},
-        "tuning": {"stages": ns, "rows_per_item": rows, "ms_per_step": ms_tune},
+        "tuning": {"stages": ns, "rows_per_item": rows, "carry": carry, "ms_per_step": ms_tune},
         "to_steady": {"wall_s": wall, "steps_done": done, "converged": int(conv.sum()),
                       "failed": int((state == lbm.FAILED).sum()), "running": int((state == lbm.RUNNING).sum()),
                       "median_steps": float(np.median(steps[conv])) if conv.any() else None,

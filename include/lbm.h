@@ -328,12 +328,16 @@ int lbm_batch_read_density(lbm_batch *b, int i, double *rho_host);
  * past it repeat the farthest point rather than wrap onto the next image. */
 int lbm_batch_profiles(lbm_batch *b, int nb, const lbm_profile_geom *geom_host, double *prof_host);
 
-/* Tile shape of the batched step: row stages per warp (3 or 4) and rows per
- * work item; lbm_batch_autotune times the candidates (stages 3, 4 x rows 32,
- * 64, 128, 256) for trial_steps steps each without advancing the state and
- * keeps the fastest. */
-int lbm_batch_set_tuning(lbm_batch *b, int stages, int rows_per_item);
-int lbm_batch_autotune(lbm_batch *b, int trial_steps, int *stages, int *rows_per_item, double *ms_per_step);
+/* Tile shape of the batched step: row stages per warp, rows per work item,
+ * and whether a row's pulled populations stay in registers from its psi pass
+ * to its collision (carry = 1: stages 2 or 3, every stage in flight) or are
+ * re-read from the stage (carry = 0: stages 3 or 4).  lbm_batch_autotune
+ * times the candidates ((3, 0), (4, 0), (2, 1), (3, 1) x rows 32, 64, 128,
+ * 256) for trial_steps steps each without advancing the state and keeps the
+ * fastest; any output pointer may be NULL. */
+int lbm_batch_set_tuning(lbm_batch *b, int stages, int rows_per_item, int carry);
+int lbm_batch_autotune(lbm_batch *b, int trial_steps, int *stages, int *rows_per_item, int *carry,
+                       double *ms_per_step);
 
 /* Total lattice nodes of the batch (-1 if b is NULL). */
 int64_t lbm_batch_nodes(lbm_batch *b);

@@ -35,7 +35,7 @@ struct BInst {
     unsigned long long seed;
     Coef<float> k;
 };
-struct BItem { int inst, x0, y0, y1; };
+struct BItem { int inst, x0, y0, y1, down, pad[3]; };   // down: walk the chunk's rows downwards
 struct BTile { int inst, tx, ty; };
 
 // Per-instance observables and convergence record (device).
@@ -68,7 +68,7 @@ constexpr size_t batch_coef_off() { return (kBatchWarps * warp_smem<NS>() + 15) 
 // One time step of every running instance.  Each warp of a CTA walks work
 // items (instance, 128-column strip, row chunk) in a grid-stride loop; the
 // instance's constants are staged in shared memory per item.
-template <int COLL, int FORC, int NS>
+template <int COLL, int FORC, int NS, bool CARRY>
 __global__ void __launch_bounds__(32 * kBatchWarps, 16 / kBatchWarps)
 k_step_batch(const float* __restrict__ fin, float* __restrict__ fout, const BInst* __restrict__ inst,
              const BItem* __restrict__ items, int n_items, const int* __restrict__ state,
@@ -93,8 +93,8 @@ k_step_batch(const float* __restrict__ fin, float* __restrict__ fout, const BIns
         if (lane < nwords) reinterpret_cast<float*>(sk)[lane] = reinterpret_cast<const float*>(&I->k)[lane];
         __syncwarp();
         unsigned bad = 0;
-        const bool ok = warp_walk<float, COLL, FORC, NS, false>(fin + I->off, fout + I->off, I->nx, I->ny, w.x0, w.y0,
-                                                                w.y1, *sk, sm, G, bad);
+        const bool ok = warp_walk<float, COLL, FORC, NS, CARRY>(fin + I->off, fout + I->off, I->nx, I->ny, w.x0,
+                                                                w.y0, w.y1, w.down != 0, *sk, sm, G, bad);
         flag_status(bad, &inst_status[w.inst]);
         __syncwarp();
         if (!ok) return;
@@ -506,7 +506,8 @@ struct lbm_batch {
     std::vector<long long> steps;
     long long total_steps = 0;
     // tuning
-    int ns = 3;                  // stages per warp (3 or 4)
+    int ns = 3;                  // stages per warp (3 or 4; 2 or 3 with carry)
+    int carry = 0;               // rows carried in registers from the psi pass to the collision
     int rows = 64;               // rows per work item
     int grid = 0;
     // graph cache
@@ -567,7 +568,7 @@ int build_items(lbm_batch* b, const int* host_state)
         for (int c = 0; c < nch; ++c) {
             const int y0 = int((long long)c * I.ny / nch), y1 = int((long long)(c + 1) * I.ny / nch);
             if (y1 <= y0) continue;
-            for (int s = 0; s < nstrips; ++s) it.push_back(BItem{i, s * 128, y0, y1});
+            for (int s = 0; s < nstrips; ++s) it.push_back(BItem{i, s * 128, y0, y1, c & 1, {0, 0, 0}});
         }
     }
     // longest items first so the grid-stride loop ends evenly
@@ -585,11 +586,11 @@ int build_items(lbm_batch* b, const int* host_state)
     return LBM_OK;
 }
 
-template <int COLL, int FORC, int NS>
+template <int COLL, int FORC, int NS, bool CARRY>
 int launch_batch_step(lbm_batch* b, const float* fin, float* fout)
 {
     constexpr size_t smem = batch_smem<NS>();
-    auto kern = k_step_batch<COLL, FORC, NS>;
+    auto kern = k_step_batch<COLL, FORC, NS, CARRY>;
     static int per_sm = 0, nsm = 0;
     if (per_sm == 0) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -608,20 +609,29 @@ int launch_batch_step(lbm_batch* b, const float* fin, float* fout)
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_E_CUDA;
 }
 
-template <int NS>
+template <int NS, bool CARRY>
 int launch_batch_scheme(lbm_batch* b, const float* fin, float* fout)
 {
-    if (b->collision == LBM_MRT) return launch_batch_step<MRT, GUO, NS>(b, fin, fout);
-    if (b->forcing == LBM_GUO) return launch_batch_step<BGK, GUO, NS>(b, fin, fout);
-    if (b->forcing == LBM_EDM) return launch_batch_step<BGK, EDM, NS>(b, fin, fout);
-    return launch_batch_step<BGK, SC, NS>(b, fin, fout);
+    if (b->collision == LBM_MRT) return launch_batch_step<MRT, GUO, NS, CARRY>(b, fin, fout);
+    if (b->forcing == LBM_GUO) return launch_batch_step<BGK, GUO, NS, CARRY>(b, fin, fout);
+    if (b->forcing == LBM_EDM) return launch_batch_step<BGK, EDM, NS, CARRY>(b, fin, fout);
+    return launch_batch_step<BGK, SC, NS, CARRY>(b, fin, fout);
+}
+
+// The step with the batch's tuning: ns stages, rows carried in registers or
+// re-read from the stage ring.
+int launch_batch_tuned(lbm_batch* b, const float* fin, float* fout)
+{
+    if (b->carry) return b->ns == 3 ? launch_batch_scheme<3, true>(b, fin, fout)
+                                    : launch_batch_scheme<2, true>(b, fin, fout);
+    return b->ns == 4 ? launch_batch_scheme<4, false>(b, fin, fout) : launch_batch_scheme<3, false>(b, fin, fout);
 }
 
 int step_once(lbm_batch* b)
 {
     const float* fin = b->f[b->cur];
     float* fout = b->f[b->cur ^ 1];
-    const int s = (b->ns == 4) ? launch_batch_scheme<4>(b, fin, fout) : launch_batch_scheme<3>(b, fin, fout);
+    const int s = launch_batch_tuned(b, fin, fout);
     if (s != LBM_OK) return s;
     b->cur ^= 1;
     return LBM_OK;
@@ -779,8 +789,10 @@ int lbm_batch_create(const lbm_batch_params* bp, const lbm_instance* inst, int n
     // one-time kernel set-up (shared-memory attribute, occupancy) outside any graph capture
     const int saved = b->nitems;
     b->nitems = 0;
-    if (s == LBM_OK) s = launch_batch_scheme<3>(b, b->f[0], b->f[1]);
-    if (s == LBM_OK) s = launch_batch_scheme<4>(b, b->f[0], b->f[1]);
+    if (s == LBM_OK) s = launch_batch_scheme<3, false>(b, b->f[0], b->f[1]);
+    if (s == LBM_OK) s = launch_batch_scheme<4, false>(b, b->f[0], b->f[1]);
+    if (s == LBM_OK) s = launch_batch_scheme<2, true>(b, b->f[0], b->f[1]);
+    if (s == LBM_OK) s = launch_batch_scheme<3, true>(b, b->f[0], b->f[1]);
     b->nitems = saved;
     if (s != LBM_OK) { lbm_batch_destroy(b); return s; }
     std::fill(b->h_state, b->h_state + b->n, (int)B_RUNNING);
@@ -1001,35 +1013,40 @@ int lbm_batch_profiles(lbm_batch* b, int nb, const lbm_profile_geom* geom_host, 
     return cuda_ok(e);
 }
 
-int lbm_batch_set_tuning(lbm_batch* b, int stages, int rows_per_item)
+int lbm_batch_set_tuning(lbm_batch* b, int stages, int rows_per_item, int carry)
 {
-    if (!b || (stages != 3 && stages != 4) || rows_per_item < 8) return LBM_E_INVALID;
+    if (!b || rows_per_item < 8) return LBM_E_INVALID;
+    if (carry ? (stages != 2 && stages != 3) : (stages != 3 && stages != 4)) return LBM_E_INVALID;
     b->ns = stages;
+    b->carry = carry ? 1 : 0;
     b->rows = rows_per_item;
     return build_items(b, b->h_state);
 }
 
-int lbm_batch_autotune(lbm_batch* b, int trial_steps, int* stages, int* rows_per_item, double* ms_per_step)
+int lbm_batch_autotune(lbm_batch* b, int trial_steps, int* stages, int* rows_per_item, int* carry,
+                       double* ms_per_step)
 {
     if (!b || trial_steps < 1) return LBM_E_INVALID;
     cudaEvent_t e0, e1;
     B_CUDA(cudaEventCreate(&e0));
     B_CUDA(cudaEventCreate(&e1));
-    const int cand_ns[2] = {3, 4};
+    const int cand_ns[4] = {3, 4, 2, 3};
+    const int cand_carry[4] = {0, 0, 1, 1};
     const int cand_rows[4] = {32, 64, 128, 256};
     float best = 3.4e38f;
-    int bns = b->ns, brows = b->rows;
+    int bns = b->ns, brows = b->rows, bcarry = b->carry;
     int status = LBM_OK;
     const int cur0 = b->cur;
-    for (int ci = 0; ci < 2 && status == LBM_OK; ++ci)
+    for (int ci = 0; ci < 4 && status == LBM_OK; ++ci)
         for (int ri = 0; ri < 4 && status == LBM_OK; ++ri) {
             b->ns = cand_ns[ci];
+            b->carry = cand_carry[ci];
             b->rows = cand_rows[ri];
             if ((status = build_items(b, b->h_state)) != LBM_OK) break;
             // trials read the current state and write the spare buffer only
             const float* fin = b->f[cur0];
             float* fout = b->f[cur0 ^ 1];
-            auto one = [&]() { return b->ns == 4 ? launch_batch_scheme<4>(b, fin, fout) : launch_batch_scheme<3>(b, fin, fout); };
+            auto one = [&]() { return launch_batch_tuned(b, fin, fout); };
             if ((status = one()) != LBM_OK) break;
             cudaEventRecord(e0, b->stream);
             for (int i = 0; i < trial_steps && status == LBM_OK; ++i) status = one();
@@ -1038,18 +1055,20 @@ int lbm_batch_autotune(lbm_batch* b, int trial_steps, int* stages, int* rows_per
             float ms = 0;
             cudaEventElapsedTime(&ms, e0, e1);
             ms /= trial_steps;
-            if (ms < best) { best = ms; bns = b->ns; brows = b->rows; }
+            if (ms < best) { best = ms; bns = b->ns; brows = b->rows; bcarry = b->carry; }
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->cur = cur0;
     b->ns = bns;
     b->rows = brows;
+    b->carry = bcarry;
     const int s = build_items(b, b->h_state);
     if (status != LBM_OK) return status;
     if (s != LBM_OK) return s;
     if (stages) *stages = bns;
     if (rows_per_item) *rows_per_item = brows;
+    if (carry) *carry = bcarry;
     if (ms_per_step) *ms_per_step = best;
     return LBM_OK;
 }

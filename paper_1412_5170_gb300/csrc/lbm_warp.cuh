@@ -97,10 +97,14 @@ __device__ __forceinline__ C halo_psi(const float* __restrict__ st, int lane, in
 // it (NS - 1 rows in flight, fewer registers, more resident warps).  Returns
 // false with ST_TIMEOUT set if a stage wait gave up (copies in flight are
 // drained, bounded).
+// down: walk the rows from y1 - 1 to y0 (walk row kr is density row y1 - kr,
+// and the psi rows y - 1 and y + 1 of the stencil trade places), so that two
+// neighbouring chunks walked in opposite directions read their shared halo
+// rows at about the same time.
 template <typename C, int COLL, int FORC, int NS, bool CARRY>
 __device__ __forceinline__ bool warp_walk(const float* __restrict__ fin, float* __restrict__ fout, int nx, int ny,
-                                          int x0, int y0, int y1, const Coef<C>& k, const WarpSmem<NS>& sm,
-                                          unsigned& G, unsigned& bad)
+                                          int x0, int y0, int y1, bool down, const Coef<C>& k,
+                                          const WarpSmem<NS>& sm, unsigned& G, unsigned& bad)
 {
     constexpr int SW = WarpSmem<NS>::SW;
     const int lane = threadIdx.x & 31;
@@ -116,7 +120,7 @@ __device__ __forceinline__ bool warp_walk(const float* __restrict__ fin, float* 
     const unsigned base = G;
     int nissued = 0;                 // walk rows whose copies have been issued
     // lane a < 9: source row of direction a for the next copy (advanced by one per copy)
-    int src_row = lane < 9 ? wrap_any(y0 - 1 - ey(lane), ny) : 0;
+    int src_row = lane < 9 ? wrap_any((down ? y1 : y0 - 1) - ey(lane), ny) : 0;
     const float* plane = fin + (lane < 9 ? lane : 0) * n;
 
     auto issue = [&]() {
@@ -137,7 +141,8 @@ __device__ __forceinline__ bool warp_walk(const float* __restrict__ fin, float* 
                 bulk_g2s(dst + 4, row + x0, unsigned(wp * sizeof(float)), bar);
                 bulk_g2s(dst + 4 + wp, row + (right_wrap ? 0 : x0 + wp), 16u, bar);
             }
-            src_row = (src_row + 1 == ny) ? 0 : src_row + 1;
+            if (down) src_row = (src_row == 0) ? ny - 1 : src_row - 1;
+            else src_row = (src_row + 1 == ny) ? 0 : src_row + 1;
         }
     };
 
@@ -186,9 +191,16 @@ __device__ __forceinline__ bool warp_walk(const float* __restrict__ fin, float* 
             if (chunk_row) pull4_warp<C>(sm.stages + ((base + kc) % NS) * 9 * SW, c0, lane, lane_hl, gc);
         }
         if (chunk_row && active) {
-            const C row_m[6] = {lm1, pm[0], pm[1], pm[2], pm[3], rm1};
+            // walk rows k-2 and k are density rows y-1 and y+1 walking up, y+1 and y-1 down
+            const C row_a[6] = {lm1, pm[0], pm[1], pm[2], pm[3], rm1};
             const C row_0[6] = {l0, pc[0], pc[1], pc[2], pc[3], r0};
-            const C row_p[6] = {lp1, pn[0], pn[1], pn[2], pn[3], rp1};
+            const C row_b[6] = {lp1, pn[0], pn[1], pn[2], pn[3], rp1};
+            C row_m[6], row_p[6];
+#pragma unroll
+            for (int j = 0; j < 6; ++j) {
+                row_m[j] = down ? row_b[j] : row_a[j];
+                row_p[j] = down ? row_a[j] : row_b[j];
+            }
             float o[9][4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -203,7 +215,7 @@ __device__ __forceinline__ bool warp_walk(const float* __restrict__ fin, float* 
 #pragma unroll
                 for (int a = 0; a < 9; ++a) o[a][j] = float(gj[a]);
             }
-            float* out = fout + (size_t)(y0 + kc - 1) * nx + x0 + c0;
+            float* out = fout + (size_t)(down ? y1 - kc : y0 + kc - 1) * nx + x0 + c0;
 #pragma unroll
             for (int a = 0; a < 9; ++a)
                 *reinterpret_cast<float4*>(out + a * n) = make_float4(o[a][0], o[a][1], o[a][2], o[a][3]);
@@ -268,7 +280,7 @@ k_step_warp(const float* __restrict__ fin, float* __restrict__ fout, int nx, int
     if (y1 <= y0) return;
     warp_init_barriers(sm);
     unsigned G = 0, bad = 0;
-    warp_walk<C, COLL, FORC, NS, CARRY>(fin, fout, nx, ny, x0, y0, y1, k, sm, G, bad);
+    warp_walk<C, COLL, FORC, NS, CARRY>(fin, fout, nx, ny, x0, y0, y1, (blockIdx.y & 1) != 0, k, sm, G, bad);
     flag_status(bad, status);
 }
 
