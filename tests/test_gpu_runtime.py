@@ -235,18 +235,22 @@ def test_every_kernel_configuration_matches_oracle(lbm):
             assert np.abs(f - ref).max() / np.abs(ref).max() < 1e-12, cid
 
 
-def test_every_fp32_configuration_matches_oracle(lbm):
+@pytest.mark.parametrize("coll,forc,nx,ny,steps", [("mrt", "guo", 260, 40, 150), ("bgk", "guo", 1028, 24, 60),
+                                                     ("bgk", "li", 2056, 20, 40), ("bgk", "edm", 260, 40, 60),
+                                                     ("bgk", "sc", 1028, 24, 60)])
+def test_every_fp32_configuration_matches_oracle(lbm, coll, forc, nx, ny, steps):
     """Each FP32-deviation kernel configuration (generic, warp-per-strip and
     block-strip tile shapes) against the FP64 oracle: per-node relative
-    density error below 2e-5 after 150 steps on a lattice with a ragged
-    last strip (260 = 2 x 128 + 4)."""
-    nx, ny, steps = 260, 40, 150
+    density error below 2e-5.  Widths give ragged last strips for every strip
+    width: 260 = 2 x 128 + 4 (one partial strip for 256 and 512 threads),
+    1028 = 1024 + 4, 2056 = 2048 + 8."""
     rv, rl = lbm.maxwell(0.8)
-    rho0 = synth.density_field(nx, ny, "droplet", rl, rv, 11.0, seed=23)
-    q = oracle.params(nx, ny, 0.8, 0.9, -0.304, 1.0, "mrt", "guo", **MRT)
+    rho0 = synth.density_field(nx, ny, "droplet", rl, rv, min(11.0, ny / 3), seed=23)
+    A, sigma = (0.0, 0.105) if forc == "li" else (-0.304, 0.0)
+    q = oracle.params(nx, ny, 0.8, 0.9, A, 1.0, coll, forc, sigma=sigma, **MRT)
     ref, _ = oracle.run(q, oracle.init_rest(rho0), steps)
     rho_ref = ref.sum(0)
-    p = lbm.make_params(nx, ny, 0.8, 0.9, -0.304, 1.0, "mrt", "guo", "fp32", **MRT)
+    p = lbm.make_params(nx, ny, 0.8, 0.9, A, 1.0, coll, forc, "fp32", sigma=sigma, **MRT)
     with lbm.Lattice(p) as lat:
         for cid, *_ in lat.configs():
             lat.config = cid
