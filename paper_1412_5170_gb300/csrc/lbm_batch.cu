@@ -65,14 +65,17 @@ constexpr int kBatchWarps = 1;   // warps (independent 128-column walkers) per C
 template <int NS>
 constexpr size_t batch_coef_off() { return (kBatchWarps * warp_smem<NS>() + 15) / 16 * 16; }
 
-// One time step of every running instance.  Each warp of a CTA walks work
-// items (instance, 128-column strip, row chunk) in a grid-stride loop; the
-// instance's constants are staged in shared memory per item.
+// One time step of every running instance.  Each warp takes work items
+// (instance, 128-column strip, row chunk) from a queue -- queue[0], a counter
+// it increments atomically, the items sorted longest first -- until none is
+// left; the instance's constants are staged in shared memory per item.  Each
+// warp then counts itself done in queue[1], and the last one clears both
+// counters, so every launch starts from zero whatever ran before it.
 template <int COLL, int FORC, int NS, bool CARRY>
 __global__ void __launch_bounds__(32 * kBatchWarps, 16 / kBatchWarps)
 k_step_batch(const float* __restrict__ fin, float* __restrict__ fout, const BInst* __restrict__ inst,
              const BItem* __restrict__ items, int n_items, const int* __restrict__ state,
-             unsigned* __restrict__ inst_status)
+             unsigned* __restrict__ inst_status, int* __restrict__ queue)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     if (!staged_alignment_ok(smem, fin, fout)) {   // flag every instance of this launch
@@ -84,8 +87,11 @@ k_step_batch(const float* __restrict__ fin, float* __restrict__ fout, const BIns
     Coef<float>* sk = reinterpret_cast<Coef<float>*>(smem + batch_coef_off<NS>()) + warp;
     warp_init_barriers(sm);
     unsigned G = 0;
-    const int nw = gridDim.x * kBatchWarps;
-    for (int it = blockIdx.x * kBatchWarps + warp; it < n_items; it += nw) {
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(&queue[0], 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) break;
         const BItem w = items[it];
         if (state[w.inst] != B_RUNNING) continue;          // uniform over the warp
         const BInst* I = inst + w.inst;
@@ -97,7 +103,14 @@ k_step_batch(const float* __restrict__ fin, float* __restrict__ fout, const BIns
                                                                 w.y0, w.y1, w.down != 0, *sk, sm, G, bad);
         flag_status(bad, &inst_status[w.inst]);
         __syncwarp();
-        if (!ok) return;
+        if (!ok) break;   // a stage wait timed out: the instance is flagged, stop this warp
+    }
+    if (lane == 0) {
+        __threadfence();
+        if (atomicAdd(&queue[1], 1) == (int)(gridDim.x * kBatchWarps) - 1) {   // the last warp done
+            atomicExch(&queue[0], 0);
+            atomicExch(&queue[1], 0);
+        }
     }
 }
 
@@ -497,6 +510,7 @@ struct lbm_batch {
     int* state = nullptr;        // device
     int* fail = nullptr;         // device
     unsigned* status = nullptr;  // device, per instance
+    int* queue = nullptr;        // device: the step's work-item counter and warps-done counter
     BObs* obs = nullptr;         // device
     double2* probe_prev = nullptr;   // device: coexistence probes at the previous check
     // pinned host mirrors
@@ -605,7 +619,8 @@ int launch_batch_step(lbm_batch* b, const float* fin, float* fout)
     if (b->nitems == 0) return LBM_OK;
     const int want = (b->nitems + kBatchWarps - 1) / kBatchWarps;
     const int grid = std::max(1, std::min(nsm * per_sm, want));
-    kern<<<grid, 32 * kBatchWarps, smem, b->stream>>>(fin, fout, b->dinst, b->items, b->nitems, b->state, b->status);
+    kern<<<grid, 32 * kBatchWarps, smem, b->stream>>>(fin, fout, b->dinst, b->items, b->nitems, b->state, b->status,
+                                                       b->queue);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_E_CUDA;
 }
 
@@ -775,6 +790,8 @@ int lbm_batch_create(const lbm_batch_params* bp, const lbm_instance* inst, int n
     if ((e = cudaMalloc(&b->state, sizeof(int) * n)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&b->fail, sizeof(int) * n)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&b->status, sizeof(unsigned) * n)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&b->queue, sizeof(int) * 2)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemset(b->queue, 0, sizeof(int) * 2)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&b->obs, sizeof(BObs) * n)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&b->probe_prev, sizeof(double2) * n)) != cudaSuccess) return fail(e);
     if ((e = cudaMallocHost(&b->h_state, sizeof(int) * n)) != cudaSuccess) return fail(e);
@@ -816,6 +833,7 @@ void lbm_batch_destroy(lbm_batch* b)
     cudaFree(b->state);
     cudaFree(b->fail);
     cudaFree(b->status);
+    cudaFree(b->queue);
     cudaFree(b->obs);
     cudaFree(b->probe_prev);
     cudaFreeHost(b->h_state);
