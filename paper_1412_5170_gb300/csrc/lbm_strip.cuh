@@ -229,7 +229,7 @@ __device__ __forceinline__ void strip_init_barriers(const StripSmem<T, C, NT, NS
 // y1 - kr instead of y0 - 1 + kr; the psi rows y - 1 and y + 1 of the
 // stencil swap ring slots).  All threads of the CTA call this with the same
 // arguments.
-template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY>
+template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY, bool HALO1 = false>
 __device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny,
                                            int x0, int y0, int y1, bool down, const Coef<C>& k,
                                            const StripSmem<T, C, NT, NS>& sm, unsigned& G, unsigned& bad)
@@ -298,7 +298,10 @@ __device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restr
                 if (active) bad |= b;
             }
             if (active) sts4(prow + 4 + c0, ps);
-            if (t == 0) prow[3] = psi_of_rho<C>(k.rho_ref + drho1<T, C>(st, SW, -1), k, bad);
+            // the two halo columns' psi: the left one by thread 0, or with HALO1 by thread 32,
+            // off the warp that issues the bulk copies (which helps some tile shapes)
+            constexpr int kLeftHalo = (HALO1 && NT >= 64) ? 32 : 0;
+            if (t == kLeftHalo) prow[3] = psi_of_rho<C>(k.rho_ref + drho1<T, C>(st, SW, -1), k, bad);
             if (t == NT - 1) prow[4 + wp] = psi_of_rho<C>(k.rho_ref + drho1<T, C>(st, SW, wp), k, bad);
         }
         if (__syncthreads_or(!ok)) return false;
@@ -358,7 +361,7 @@ __device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restr
 
 // One lattice, grid (strips, row chunks).  MINB > 1 asks the compiler to fit
 // MINB CTAs per SM in the register file (at the price of spills if needed).
-template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY, int MINB>
+template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY, int MINB, bool HALO1>
 __global__ void __launch_bounds__(NT, MINB)
 k_step_strip(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, int nchunks, Coef<C> k,
              unsigned* __restrict__ status)
@@ -375,8 +378,8 @@ k_step_strip(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, in
     if (y1 <= y0) return;
     strip_init_barriers(sm);
     unsigned G = 0, bad = 0;
-    strip_walk<T, C, COLL, FORC, NT, NS, CARRY>(fin, fout, nx, ny, x0, y0, y1, (blockIdx.y & 1) != 0, k, sm, G,
-                                                bad);
+    strip_walk<T, C, COLL, FORC, NT, NS, CARRY, HALO1>(fin, fout, nx, ny, x0, y0, y1, (blockIdx.y & 1) != 0, k, sm,
+                                                       G, bad);
     flag_status(bad, status);
 }
 
@@ -389,11 +392,11 @@ constexpr size_t strip_smem()
 // One launch over the whole lattice: strips of 4*NT columns, and as many row
 // chunks as fill every resident CTA slot once (one wave), but no chunk shorter
 // than 16 rows, so the two halo rows per chunk stay a small overhead.
-template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY, int MINB>
+template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY, int MINB, bool HALO1>
 int launch_strip_cfg(const lbm_params* p, const void* fin, void* fout, unsigned* status, cudaStream_t s)
 {
     constexpr size_t smem = strip_smem<T, C, NT, NS>();
-    auto kern = k_step_strip<T, C, COLL, FORC, NT, NS, CARRY, MINB>;
+    auto kern = k_step_strip<T, C, COLL, FORC, NT, NS, CARRY, MINB, HALO1>;
     static int per_sm = 0, nsm = 0;    // per instantiation (one device per process)
     if (per_sm == 0) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -413,14 +416,18 @@ int launch_strip_cfg(const lbm_params* p, const void* fin, void* fout, unsigned*
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_E_CUDA;
 }
 
-template <typename T, typename C, int NT, int NS, bool CARRY = false, int MINB = 1>
+template <typename T, typename C, int NT, int NS, bool CARRY = false, int MINB = 1, bool HALO1 = false>
 int launch_strip_scheme(const lbm_params* p, const void* fin, void* fout, unsigned* status, cudaStream_t s)
 {
-    if (p->collision == LBM_MRT) return launch_strip_cfg<T, C, MRT, GUO, NT, NS, CARRY, MINB>(p, fin, fout, status, s);
-    if (p->forcing == LBM_GUO) return launch_strip_cfg<T, C, BGK, GUO, NT, NS, CARRY, MINB>(p, fin, fout, status, s);
-    if (p->forcing == LBM_EDM) return launch_strip_cfg<T, C, BGK, EDM, NT, NS, CARRY, MINB>(p, fin, fout, status, s);
-    if (p->forcing == LBM_LI) return launch_strip_cfg<T, C, BGK, LI, NT, NS, CARRY, MINB>(p, fin, fout, status, s);
-    return launch_strip_cfg<T, C, BGK, SC, NT, NS, CARRY, MINB>(p, fin, fout, status, s);
+    if (p->collision == LBM_MRT)
+        return launch_strip_cfg<T, C, MRT, GUO, NT, NS, CARRY, MINB, HALO1>(p, fin, fout, status, s);
+    if (p->forcing == LBM_GUO)
+        return launch_strip_cfg<T, C, BGK, GUO, NT, NS, CARRY, MINB, HALO1>(p, fin, fout, status, s);
+    if (p->forcing == LBM_EDM)
+        return launch_strip_cfg<T, C, BGK, EDM, NT, NS, CARRY, MINB, HALO1>(p, fin, fout, status, s);
+    if (p->forcing == LBM_LI)
+        return launch_strip_cfg<T, C, BGK, LI, NT, NS, CARRY, MINB, HALO1>(p, fin, fout, status, s);
+    return launch_strip_cfg<T, C, BGK, SC, NT, NS, CARRY, MINB, HALO1>(p, fin, fout, status, s);
 }
 
 }  // namespace lbm

@@ -11,7 +11,8 @@ using namespace lbm;
 // kind 4 the register-carrying block strip held to 128 registers so that
 // 16 warps share an SM (4 CTAs of 128 threads or 2 of 256).
 extern const StripConfig kStripF32[] = {{128, 3, 3}, {64, 3, 3}, {64, 4, 3}, {128, 4, 3},
-                                        {32, 3, 1}, {32, 4, 1}, {128, 3, 0}, {128, 2, 4}, {256, 2, 4}, {512, 2, 4}};
+                                        {32, 3, 1}, {32, 4, 1}, {128, 3, 0}, {128, 2, 4}, {256, 2, 4}, {512, 2, 4},
+                                        {128, 3, 3}, {256, 2, 4}};
 extern const int kStripF32Count = sizeof(kStripF32) / sizeof(kStripF32[0]);
 
 int lbm_strip_launch_f32(const lbm_params* p, int cfg, const void* fin, void* fout, unsigned* st, cudaStream_t s)
@@ -29,6 +30,9 @@ int lbm_strip_launch_f32(const lbm_params* p, int cfg, const void* fin, void* fo
     case 7: return launch_strip_scheme<float, float, 128, 2, true, 4>(p, fin, fout, st, s);
     case 8: return launch_strip_scheme<float, float, 256, 2, true, 2>(p, fin, fout, st, s);
     case 9: return launch_strip_scheme<float, float, 512, 2, true, 1>(p, fin, fout, st, s);
+    // the same tile shapes as 0 and 8 with the left halo column's psi on thread 32
+    case 10: return launch_strip_scheme<float, float, 128, 3, true, 3, true>(p, fin, fout, st, s);
+    case 11: return launch_strip_scheme<float, float, 256, 2, true, 2, true>(p, fin, fout, st, s);
     default: return LBM_E_INVALID;
     }
 }
