@@ -14,7 +14,9 @@
  *   v             u + F/(2 rho) (Sec. 3.2)
  *   collision     BGK (Eq. 1) with Guo (Eq. 23), exact-difference (Eq. 22)
  *                 or Shan-Chen velocity-shift (Eqs. 20-21) forcing, or MRT
- *                 with Guo's source in moment space (Eqs. 34-35)
+ *                 with Guo's source in moment space (Eqs. 34-35); and Li et
+ *                 al.'s model for comparison (Sec. 4.3, Eqs. 31-32: BGK,
+ *                 Eq. 4 force, Guo's source with a shifted velocity)
  *   streaming     pull, periodic in x and y (Eq. 1 / Eq. 36)
  *
  * Conventions shared by every entry point:
