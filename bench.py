@@ -43,13 +43,8 @@ SEED = 20141217 + 2 * 1000
 # kernel sources it was taken from, the kernel configuration id and the
 # lattice side; when any of them changes the entry no longer matches and
 # traffic is null.
-# (Configurations 9 and 12 are the 256-thread two-stage kernel with the left
-# halo column's psi on thread 0 and on thread 32; their captures were taken
-# before the two were put side by side in the configuration table, from
-# sources that compile to the same kernels.)
 TRAFFIC_CAPTURES: dict = {
-    ("176e9309e6a39f63", 9, 4096): (608.67e6 + 548.07e6),
-    ("176e9309e6a39f63", 12, 4096): (609.41e6 + 548.74e6),
+    ("c822e51cfad157f1", 9, 4096): (609.85e6 + 549.15e6),
 }
 # Sources of the block-strip step kernel (its configuration table included).
 KERNEL_SOURCES = ["paper_1412_5170_gb300/csrc/lbm_strip.cuh", "paper_1412_5170_gb300/csrc/lbm_strip_f32.cu",

@@ -249,7 +249,8 @@ __device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restr
     const bool lsm = lane == 0, rsm = (lane == 31) || (c0 + 4 == wp);   // neighbours from shared memory
     int nissued = 0;
 
-    // Warp 0 issues the nine segment copies of the next walk row into its stage.
+    // Warp 0 issues the nine segment copies of the next walk row into its stage
+    // (27 at the periodic seam), one per lane.
     auto issue = [&]() {
         const int kr = nissued++;
         if (t >= 32) return;
@@ -258,18 +259,22 @@ __device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restr
         T* st = sm.stages + (g % NS) * 9 * SW;
         if (t == 0) mbar_arrive_expect_tx(bar, stage_bytes);
         __syncwarp();
-        if (t < 9) {
+        const bool seam = left_wrap || right_wrap;   // uniform over the CTA
+        if (t < (seam ? 27 : 9)) {
+            // one copy per lane: direction a = t (or t / 3 at the periodic seam, where each
+            // segment splits into its left halo, its body and its right halo, piece t % 3)
             fence_proxy_async();   // order earlier generic reads of this slot before the async writes
-            const int a = t;
+            const int a = seam ? t / 3 : t;
             const int r = wrap_any((down ? y1 - kr : y0 - 1 + kr) - ey(a), ny);
             const T* row = fin + a * n + (size_t)r * nx;
             T* dst = st + a * SW;
-            if (!left_wrap && !right_wrap) {
+            if (!seam) {
                 bulk_g2s(dst, row + x0 - 4, unsigned((wp + 8) * sizeof(T)), bar);
             } else {
-                bulk_g2s(dst, row + (left_wrap ? nx - 4 : x0 - 4), unsigned(4 * sizeof(T)), bar);
-                bulk_g2s(dst + 4, row + x0, unsigned(wp * sizeof(T)), bar);
-                bulk_g2s(dst + 4 + wp, row + (right_wrap ? 0 : x0 + wp), unsigned(4 * sizeof(T)), bar);
+                const int piece = t - 3 * a;
+                if (piece == 0) bulk_g2s(dst, row + (left_wrap ? nx - 4 : x0 - 4), unsigned(4 * sizeof(T)), bar);
+                else if (piece == 1) bulk_g2s(dst + 4, row + x0, unsigned(wp * sizeof(T)), bar);
+                else bulk_g2s(dst + 4 + wp, row + (right_wrap ? 0 : x0 + wp), unsigned(4 * sizeof(T)), bar);
             }
         }
     };
