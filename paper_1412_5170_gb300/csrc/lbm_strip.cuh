@@ -229,7 +229,8 @@ __device__ __forceinline__ void strip_init_barriers(const StripSmem<T, C, NT, NS
 // y1 - kr instead of y0 - 1 + kr; the psi rows y - 1 and y + 1 of the
 // stencil swap ring slots).  All threads of the CTA call this with the same
 // arguments.
-template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY, bool HALO1 = false>
+template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY, bool HALO1 = false,
+          bool PSEAM = false>
 __device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny,
                                            int x0, int y0, int y1, bool down, const Coef<C>& k,
                                            const StripSmem<T, C, NT, NS>& sm, unsigned& G, unsigned& bad)
@@ -249,8 +250,9 @@ __device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restr
     const bool lsm = lane == 0, rsm = (lane == 31) || (c0 + 4 == wp);   // neighbours from shared memory
     int nissued = 0;
 
-    // Warp 0 issues the nine segment copies of the next walk row into its stage
-    // (27 at the periodic seam), one per lane.
+    // Warp 0 issues the nine segment copies of the next walk row into its stage,
+    // one per lane; at the periodic seam each splits in three, issued by the
+    // same lane or, with PSEAM, by three lanes.
     auto issue = [&]() {
         const int kr = nissued++;
         if (t >= 32) return;
@@ -260,21 +262,31 @@ __device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restr
         if (t == 0) mbar_arrive_expect_tx(bar, stage_bytes);
         __syncwarp();
         const bool seam = left_wrap || right_wrap;   // uniform over the CTA
-        if (t < (seam ? 27 : 9)) {
-            // one copy per lane: direction a = t (or t / 3 at the periodic seam, where each
-            // segment splits into its left halo, its body and its right halo, piece t % 3)
+        if (PSEAM && seam) {
+            // one copy per lane at the periodic seam: direction t / 3, piece t % 3 (the
+            // segment's left halo, its body, its right halo)
+            if (t < 27) {
+                fence_proxy_async();   // order earlier generic reads of this slot before the async writes
+                const int a = t / 3, piece = t - 3 * a;
+                const int r = wrap_any((down ? y1 - kr : y0 - 1 + kr) - ey(a), ny);
+                const T* row = fin + a * n + (size_t)r * nx;
+                T* dst = st + a * SW;
+                if (piece == 0) bulk_g2s(dst, row + (left_wrap ? nx - 4 : x0 - 4), unsigned(4 * sizeof(T)), bar);
+                else if (piece == 1) bulk_g2s(dst + 4, row + x0, unsigned(wp * sizeof(T)), bar);
+                else bulk_g2s(dst + 4 + wp, row + (right_wrap ? 0 : x0 + wp), unsigned(4 * sizeof(T)), bar);
+            }
+        } else if (t < 9) {
             fence_proxy_async();   // order earlier generic reads of this slot before the async writes
-            const int a = seam ? t / 3 : t;
+            const int a = t;
             const int r = wrap_any((down ? y1 - kr : y0 - 1 + kr) - ey(a), ny);
             const T* row = fin + a * n + (size_t)r * nx;
             T* dst = st + a * SW;
             if (!seam) {
                 bulk_g2s(dst, row + x0 - 4, unsigned((wp + 8) * sizeof(T)), bar);
             } else {
-                const int piece = t - 3 * a;
-                if (piece == 0) bulk_g2s(dst, row + (left_wrap ? nx - 4 : x0 - 4), unsigned(4 * sizeof(T)), bar);
-                else if (piece == 1) bulk_g2s(dst + 4, row + x0, unsigned(wp * sizeof(T)), bar);
-                else bulk_g2s(dst + 4 + wp, row + (right_wrap ? 0 : x0 + wp), unsigned(4 * sizeof(T)), bar);
+                bulk_g2s(dst, row + (left_wrap ? nx - 4 : x0 - 4), unsigned(4 * sizeof(T)), bar);
+                bulk_g2s(dst + 4, row + x0, unsigned(wp * sizeof(T)), bar);
+                bulk_g2s(dst + 4 + wp, row + (right_wrap ? 0 : x0 + wp), unsigned(4 * sizeof(T)), bar);
             }
         }
     };
@@ -366,7 +378,7 @@ __device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restr
 
 // One lattice, grid (strips, row chunks).  MINB > 1 asks the compiler to fit
 // MINB CTAs per SM in the register file (at the price of spills if needed).
-template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY, int MINB, bool HALO1>
+template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY, int MINB, bool HALO1, bool PSEAM>
 __global__ void __launch_bounds__(NT, MINB)
 k_step_strip(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, int nchunks, Coef<C> k,
              unsigned* __restrict__ status)
@@ -383,8 +395,8 @@ k_step_strip(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, in
     if (y1 <= y0) return;
     strip_init_barriers(sm);
     unsigned G = 0, bad = 0;
-    strip_walk<T, C, COLL, FORC, NT, NS, CARRY, HALO1>(fin, fout, nx, ny, x0, y0, y1, (blockIdx.y & 1) != 0, k, sm,
-                                                       G, bad);
+    strip_walk<T, C, COLL, FORC, NT, NS, CARRY, HALO1, PSEAM>(fin, fout, nx, ny, x0, y0, y1, (blockIdx.y & 1) != 0,
+                                                              k, sm, G, bad);
     flag_status(bad, status);
 }
 
@@ -397,11 +409,11 @@ constexpr size_t strip_smem()
 // One launch over the whole lattice: strips of 4*NT columns, and as many row
 // chunks as fill every resident CTA slot once (one wave), but no chunk shorter
 // than 16 rows, so the two halo rows per chunk stay a small overhead.
-template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY, int MINB, bool HALO1>
+template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY, int MINB, bool HALO1, bool PSEAM>
 int launch_strip_cfg(const lbm_params* p, const void* fin, void* fout, unsigned* status, cudaStream_t s)
 {
     constexpr size_t smem = strip_smem<T, C, NT, NS>();
-    auto kern = k_step_strip<T, C, COLL, FORC, NT, NS, CARRY, MINB, HALO1>;
+    auto kern = k_step_strip<T, C, COLL, FORC, NT, NS, CARRY, MINB, HALO1, PSEAM>;
     static int per_sm = 0, nsm = 0;    // per instantiation (one device per process)
     if (per_sm == 0) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -421,18 +433,19 @@ int launch_strip_cfg(const lbm_params* p, const void* fin, void* fout, unsigned*
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_E_CUDA;
 }
 
-template <typename T, typename C, int NT, int NS, bool CARRY = false, int MINB = 1, bool HALO1 = false>
+template <typename T, typename C, int NT, int NS, bool CARRY = false, int MINB = 1, bool HALO1 = false,
+          bool PSEAM = false>
 int launch_strip_scheme(const lbm_params* p, const void* fin, void* fout, unsigned* status, cudaStream_t s)
 {
     if (p->collision == LBM_MRT)
-        return launch_strip_cfg<T, C, MRT, GUO, NT, NS, CARRY, MINB, HALO1>(p, fin, fout, status, s);
+        return launch_strip_cfg<T, C, MRT, GUO, NT, NS, CARRY, MINB, HALO1, PSEAM>(p, fin, fout, status, s);
     if (p->forcing == LBM_GUO)
-        return launch_strip_cfg<T, C, BGK, GUO, NT, NS, CARRY, MINB, HALO1>(p, fin, fout, status, s);
+        return launch_strip_cfg<T, C, BGK, GUO, NT, NS, CARRY, MINB, HALO1, PSEAM>(p, fin, fout, status, s);
     if (p->forcing == LBM_EDM)
-        return launch_strip_cfg<T, C, BGK, EDM, NT, NS, CARRY, MINB, HALO1>(p, fin, fout, status, s);
+        return launch_strip_cfg<T, C, BGK, EDM, NT, NS, CARRY, MINB, HALO1, PSEAM>(p, fin, fout, status, s);
     if (p->forcing == LBM_LI)
-        return launch_strip_cfg<T, C, BGK, LI, NT, NS, CARRY, MINB, HALO1>(p, fin, fout, status, s);
-    return launch_strip_cfg<T, C, BGK, SC, NT, NS, CARRY, MINB, HALO1>(p, fin, fout, status, s);
+        return launch_strip_cfg<T, C, BGK, LI, NT, NS, CARRY, MINB, HALO1, PSEAM>(p, fin, fout, status, s);
+    return launch_strip_cfg<T, C, BGK, SC, NT, NS, CARRY, MINB, HALO1, PSEAM>(p, fin, fout, status, s);
 }
 
 }  // namespace lbm
