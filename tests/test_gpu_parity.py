@@ -2,14 +2,14 @@
 element, on seeded inputs.
 
 Tolerances:
-* FP64: max |f_gpu - f_oracle| / max |f| < 1e-12 (spec bar: max
+* FP64: max |f_gpu - f_oracle| / max |f| < 1e-12 (the FP64 parity bar: max
   |drho|/rho < 1e-12 after 1000 steps; reassociation and FMA contraction are
   the only differences).
 * FP32 deviations: per-step rounding of float arithmetic on deviations
   f - w rho_ref gives a relative density error of order 1e-7 per step that
   the dissipative dynamics does not amplify; the element-wise bar after
   200 steps is 2e-5 on rho, and the converged coexistence densities must
-  agree to 1e-4 relative with Us_max within 5 % (spec bars).
+  agree to 1e-4 relative with Us_max within 5 % (the FP32 bars).
 """
 import numpy as np
 import pytest
@@ -101,7 +101,7 @@ def test_strip_and_generic_agree(lbm):
 
 
 def test_fp32_flat_interface_coexistence(lbm):
-    """North-star FP32 bar on the 64x64 slab (BGK + Guo, T/Tc = 0.8): after
+    """The FP32 bar on the 64x64 slab (BGK + Guo, T/Tc = 0.8): after
     10000 steps the FP32-deviation coexistence densities agree with the FP64
     oracle to 1e-4 relative.  (A converged flat interface has spurious
     velocities of ~1e-9, below FP32 resolution; Us_max is compared on the
@@ -127,7 +127,7 @@ def test_fp32_flat_interface_coexistence(lbm):
 
 @pytest.mark.parametrize("coll", ["bgk", "mrt"])
 def test_fp32_droplet_coexistence_and_spurious_velocity(lbm, coll):
-    """North-star FP32 bar on a curved interface: droplet R = 16 on 64x64,
+    """The FP32 bar on a curved interface: droplet R = 16 on 64x64,
     T/Tc = 0.8, tau = 1, 10000 steps.  Liquid (centre) and vapour (corner)
     densities within 1e-4 relative of the FP64 oracle, Us_max within 5 %."""
     nx = ny = 64
