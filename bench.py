@@ -507,9 +507,9 @@ def run_batch(args):
                       "failed": int((state == lbm.FAILED).sum()), "running": int((state == lbm.RUNNING).sum()),
                       "median_steps": float(np.median(steps[conv])) if conv.any() else None,
                       "node_steps_per_s": node_steps / wall},
-        "config": {"workload": "batched sweep, 512 instances: side U{64..512}, T/Tc U[.5,.9], tau U[.55,1.2], "
+        "config": {"workload": "batched sweep, %d instances: side U{64..512}, T/Tc U[.5,.9], tau U[.55,1.2], "
                                "K U[1/16,1], R U[10, side/4], droplet or slab; MRT+Guo, A=%g, FP32 deviations; "
-                               "criterion: coexistence probes change < %g per 1000 steps" % (args.ws_A, args.ws_tol)},
+                               "criterion: coexistence probes change < %g per 1000 steps" % (args.batch_n, args.ws_A, args.ws_tol)},
     }
     print(json.dumps(line), flush=True)
 

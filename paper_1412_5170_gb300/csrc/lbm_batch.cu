@@ -554,9 +554,10 @@ void drop_graphs(lbm_batch* b)
 // b->rows rows (never under 8).
 // Work items of the running instances: 128-column strips cut into row chunks
 // of about b->rows rows.  When the running instances hold too few strip rows
-// to give every SM about eight items at that length (the tail of a run, when
-// a few instances remain), the chunks shrink -- down to 16 rows -- so a step
-// is spread over more warps and its latency (one row walk) shortens.
+// to give every SM about sixteen items at that length (small batches, and
+// the tail of a run when a few instances remain), the chunks shrink -- down
+// to 16 rows -- so a step is spread over more warps (up to the 14-16 a
+// batched-step SM holds) and its latency (one row walk) shortens.
 int build_items(lbm_batch* b, const int* host_state)
 {
     static int nsm = 0;
@@ -571,7 +572,7 @@ int build_items(lbm_batch* b, const int* host_state)
         const BInst& I = b->hinst[i];
         strip_rows += (long long)((I.nx + 127) / 128) * I.ny;
     }
-    const long long target = 8LL * nsm;
+    const long long target = 16LL * nsm;
     const int rows = (int)std::max<long long>(std::min<long long>(b->rows, strip_rows / target), std::min(16, b->rows));
     std::vector<BItem> it;
     for (int i = 0; i < b->n; ++i) {
