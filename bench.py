@@ -385,6 +385,7 @@ def run_warmstart(args):
                             **MRT)
         with lbm.Lattice(p) as lat:
             lat.init_preset(d["kind"], d["size"], seed=d["seed"])
+            lat.autotune(3)   # the fastest FP64 kernel for this lattice (the state does not advance)
             torch.cuda.synchronize()
             ts = time.perf_counter()
             st_code, steps, probes = fp64_run_to_steady(lat, d["kind"], args.ws_tol, 1000, args.ws_max_steps)
