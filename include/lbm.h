@@ -205,7 +205,8 @@ int lbm_load(lbm_ctx *ctx, const char *path);
  * first strip configuration; LBM_E_UNSUPPORTED if the lattice does not
  * allow it); -1 restores the automatic choice: the strip kernel where it
  * applies (for FP32 lattices at least 1024 wide its 256-thread, two-stage
- * configuration), else the generic kernel.  lbm_autotune picks by timing. */
+ * configuration) and its strips and row chunks can give every SM a CTA,
+ * else the generic kernel.  lbm_autotune picks by timing. */
 int lbm_get_variant(lbm_ctx *ctx, int *variant);
 int lbm_set_variant(lbm_ctx *ctx, int variant);
 

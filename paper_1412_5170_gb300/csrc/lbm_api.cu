@@ -3,6 +3,7 @@
 // population I/O and checkpoints.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -103,18 +104,32 @@ void launch_generic_scheme(lbm_ctx* c, const void* fin, void* fout)
 // Without autotuning: the strip kernel where it applies -- for FP32 lattices
 // at least 1024 wide the 256-thread, two-stage carried configuration (the
 // fastest measured on large lattices), otherwise the first strip
-// configuration -- else the generic kernel.
+// configuration -- unless its strips and row chunks (at least 16 rows each)
+// cannot give every SM a CTA, as on small lattices, where the generic
+// kernel's 32 x 8 tiles spread wider; else the generic kernel.
 int default_config(const lbm_params& p)
 {
     if (!lbm_strip_supported(&p)) return 0;
+    int cfg = 1;
     if (p.precision == LBM_FP32_DEV && p.nx >= 1024) {
         const int n = lbm_strip_config_count(p.precision);
         for (int i = 0; i < n; ++i) {
             const StripConfig sc = lbm_strip_config(p.precision, i);
-            if (sc.threads == 256 && sc.stages == 2) return i + 1;
+            if (sc.threads == 256 && sc.stages == 2) { cfg = i + 1; break; }
         }
     }
-    return 1;
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+            nsm = 1;
+    }
+    const StripConfig sc = lbm_strip_config(p.precision, cfg - 1);
+    const long long width = 4LL * sc.threads;
+    const long long strips = (p.nx + width - 1) / width;
+    if (strips * std::max(1, p.ny / 16) < nsm) return 0;
+    return cfg;
 }
 
 int n_configs(const lbm_params& p) { return 1 + (lbm_strip_supported(&p) ? lbm_strip_config_count(p.precision) : 0); }

@@ -207,13 +207,17 @@ def test_workspace_from_library_allocation(lbm):
 
 def test_variant_selection(lbm):
     with lattice(lbm, 30, 30) as lat:
-        assert lat.variant == 0
+        assert lat.variant == 0                  # nx % 4 != 0: the generic kernel only
         with pytest.raises(lbm.LbmError):
             lat.variant = 1
     with lattice(lbm, 64, 30) as lat:
+        assert lat.variant == 0                  # too few strips x chunks to give every SM a CTA
+        lat.variant = 1
         assert lat.variant == 1
-        lat.variant = 0
+        lat.variant = -1
         assert lat.variant == 0
+    with lattice(lbm, 1024, 2560) as lat:        # 4 strips x 160 chunks: the strip kernel
+        assert lat.variant == 1
 
 
 def test_every_kernel_configuration_matches_oracle(lbm):
