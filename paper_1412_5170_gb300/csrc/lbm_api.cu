@@ -197,7 +197,15 @@ double rho_ref_eff(const lbm_params& p)
 template <typename T>
 void launch_init_rest(lbm_ctx* c, const double* rho0)
 {
-    k_init_rest<T><<<1024, 256, 0, c->stream>>>(rho0, (T*)c->f[c->cur], c->p.nx, c->p.ny, rho_ref_eff(c->p));
+    if constexpr (sizeof(T) == sizeof(float)) {
+        // the FP64 v_x field doubles as the float deviation scratch (n floats fit in n doubles)
+        float* dev = reinterpret_cast<float*>(c->vx);
+        const size_t n = (size_t)c->p.nx * c->p.ny;
+        k_init_dev_f32<<<1024, 256, 0, c->stream>>>(rho0, dev, n, rho_ref_eff(c->p));
+        k_init_rest_f32<<<1024, 256, 0, c->stream>>>(dev, (float*)c->f[c->cur], c->p.nx, c->p.ny);
+    } else {
+        k_init_rest<T><<<1024, 256, 0, c->stream>>>(rho0, (T*)c->f[c->cur], c->p.nx, c->p.ny, rho_ref_eff(c->p));
+    }
 }
 
 template <typename T>

@@ -294,6 +294,29 @@ __global__ void k_init_rest(const double* __restrict__ rho0, T* __restrict__ fs,
     }
 }
 
+// FP32-deviation initial state in two passes, off the FP64 pipe: the density
+// deviation of every node once, dev = float(rho0 - rho_ref), then
+// g_a(x) = w_a dev(x + e_a) (the stored f*_a(x) of a start at rest).
+static __global__ void k_init_dev_f32(const double* __restrict__ rho0, float* __restrict__ dev, size_t n, double rho_ref)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dev[i] = float(rho0[i] - rho_ref);
+}
+
+static __global__ void k_init_rest_f32(const float* __restrict__ dev, float* __restrict__ fs, int nx, int ny)
+{
+    const size_t n = (size_t)nx * ny;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = int(i % nx), y = int(i / nx);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            const int xs = ex(a) > 0 ? inc1(x, nx) : (ex(a) < 0 ? dec1(x, nx) : x);
+            const int ys = ey(a) > 0 ? inc1(y, ny) : (ey(a) < 0 ? dec1(y, ny) : y);
+            fs[a * n + i] = wt<float>(a) * dev[(size_t)ys * nx + xs];
+        }
+    }
+}
+
 // One plane a: stored <- post-streaming (dir = +1) or post-streaming <- stored (dir = -1).
 template <typename T>
 __global__ void k_plane_convert(T* __restrict__ fs, double* __restrict__ plane, int a, int nx, int ny,
