@@ -639,6 +639,55 @@ def run_coexistence(args):
     print(json.dumps(line), flush=True)
 
 
+def run_laplace(args):
+    """Laplace's law on static gas bubbles (the Table 3 / Table 4 setups):
+    bubbles of R = 15 .. 35 on 128^2 at T/Tc = 0.6, FP64, 30 000 steps; the
+    pressure jump dp = p0(rho_g) - p0(rho_l) of the K-scaled EOS (Eq. 30) at
+    the centre and corner probes against 1/R_eq, R_eq from the mass deficit of
+    the bubble.  The slope is the surface tension; a straight line through
+    the origin is Laplace's law."""
+    import numpy as np
+
+    from paper_1412_5170_gb300 import lbm
+
+    T = 0.6
+    Tabs = T * lbm.tc()
+
+    def p0(rho, K):
+        return K * (rho * Tabs * (1 + rho + rho ** 2 - rho ** 3) / (1 - rho) ** 3 - rho ** 2)
+
+    cases = [("guo", -0.9, 0.5, 1.5, 0.01059), ("guo", -0.9, 0.5, 0.7, 0.010368),
+             ("edm", -0.26, 0.5, 1.5, 0.01241), ("edm", -0.26, 0.5, 0.7, 0.013635),
+             ("guo", -0.84, 1.0, 1.0, None)]
+    rows = []
+    t0 = time.perf_counter()
+    for forc, A, K, tau, paper_sigma in cases:
+        pts = []
+        for R in (15.0, 20.0, 25.0, 30.0, 35.0):
+            p = lbm.make_params(128, 128, T, tau, A, K, "bgk", forc, "fp64")
+            with lbm.Lattice(p) as lat:
+                lat.init_preset("bubble", R, seed=1)
+                lat.autotune(3)
+                lat.step(args.laplace_steps)
+                st = lat.stats()
+                rho = lat.read_moments()[0]
+            rg, rl = st["rho_center"], st["rho_corner"]
+            r_eq = float(np.sqrt(np.sum(rl - rho) / (np.pi * (rl - rg))))
+            pts.append((r_eq, p0(rg, K) - p0(rl, K), rg, rl, st["status"]))
+        x = np.array([1.0 / q[0] for q in pts])
+        y = np.array([q[1] for q in pts])
+        slope, icpt = np.polyfit(x, y, 1)
+        r2 = 1.0 - np.sum((y - (slope * x + icpt)) ** 2) / np.sum((y - y.mean()) ** 2)
+        rows.append(dict(forcing=forc, A=A, K=K, tau=tau, sigma=float(slope), intercept=float(icpt), r2=float(r2),
+                         paper_sigma=paper_sigma, points=[[round(q[0], 3), q[1], q[2], q[3], q[4]] for q in pts]))
+        print("  %s A %g K %g tau %g: sigma %.5g intercept %.2e r2 %.6f (paper %s)" % (
+            forc, A, K, tau, slope, icpt, r2, paper_sigma), file=sys.stderr, flush=True)
+    line = {"metric": "surface tension from Laplace's law, static bubbles", "unit": "lattice units",
+            "rows": rows, "steps": args.laplace_steps, "wall_s": time.perf_counter() - t0,
+            "config": {"workload": "gas bubbles R = 15..35 on 128x128, T/Tc = 0.6, BGK, FP64"}}
+    print(json.dumps(line), flush=True)
+
+
 def fp64_run_to_steady(lat, kind, tol, every, max_steps):
     """Cold single-lattice run until both coexistence densities (centre and
     corner, or mid and edge row for a slab) change by less than tol relative
@@ -666,7 +715,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="throughput", choices=["throughput", "warmstart", "sweep", "coexistence", "batch"])
+    ap.add_argument("--mode", default="throughput", choices=["throughput", "warmstart", "sweep", "coexistence", "batch", "laplace"])
+    ap.add_argument("--laplace-steps", type=int, default=30000)
     ap.add_argument("--batch-n", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--coex-steps", type=int, default=40000)
@@ -703,6 +753,8 @@ def main():
         run_coexistence(args)
     elif args.mode == "batch":
         run_batch(args)
+    elif args.mode == "laplace":
+        run_laplace(args)
     else:
         run_ours(args)
 
