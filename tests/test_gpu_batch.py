@@ -17,21 +17,21 @@ def instances():
             dict(nx=260, ny=36, kind="bubble", T_over_Tc=0.8, tau=1.2, A=-0.304, K=1.0, size=12.0, seed=4)]
 
 
-@pytest.mark.parametrize("coll", ["bgk", "mrt"])
-def test_batch_matches_single_lattice_path(lbm, coll):
+@pytest.mark.parametrize("coll,forc", [("bgk", "guo"), ("mrt", "guo"), ("bgk", "edm"), ("bgk", "sc")])
+def test_batch_matches_single_lattice_path(lbm, coll, forc):
     """Every instance of a batch evolves as the same lattice run alone with the
     warp strip kernel.  The per-node arithmetic is the same; the initial fields
     differ in the last bits (the batch evaluates the tanh preset on the device,
     the single-lattice call on the host) and the vapour's early transient
     amplifies that, so the bar is the FP32 element-wise bar."""
     inst = instances()
-    with lbm.Batch(inst, collision=coll) as b:
+    with lbm.Batch(inst, collision=coll, forcing=forc) as b:
         b.init()
         b.step(57)
         got = [b.read_density(i) for i in range(len(inst))]
     for i, d in enumerate(inst):
         nx, ny = d.get("nx", d.get("side")), d.get("ny", d.get("side"))
-        p = lbm.make_params(nx, ny, d["T_over_Tc"], d["tau"], d["A"], d["K"], coll, "guo", "fp32",
+        p = lbm.make_params(nx, ny, d["T_over_Tc"], d["tau"], d["A"], d["K"], coll, forc, "fp32",
                             s_e=0.8, s_eps=0.8, s_q=1.1)
         with lbm.Lattice(p) as lat:
             lat.config = 1
@@ -194,3 +194,10 @@ def test_batch_autotune_keeps_state(lbm):
         after = [b.read_density(i) for i in range(len(inst))]
     for x, y in zip(before, after):
         assert np.array_equal(x, y)
+
+
+def test_batch_rejects_li_forcing(lbm):
+    """The batch carries no sigma: Li et al.'s model runs on single lattices."""
+    inst = instances()[:1]
+    with pytest.raises(lbm.LbmError):
+        lbm.Batch(inst, collision="bgk", forcing="li")
