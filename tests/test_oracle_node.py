@@ -124,3 +124,25 @@ def test_mrt_nonconserved_rates_matter_only_off_equilibrium(orc):
     for se, sq in itertools.product((0.8, 1.3), (1.1, 1.7)):
         p = orc.params(4, 4, .7, 0.8, -.1, 1, "mrt", "guo", s_e=se, s_eps=se, s_q=sq)
         np.testing.assert_allclose(orc.collide_node(p, f, r, *(j / r), 0.0, 0.0), f, atol=1e-16)
+
+
+def test_li_collision_moments(orc):
+    """Eq. 31 at one node: the collision conserves mass, adds F to the
+    momentum exactly once, and its second moment carries, beyond Guo's,
+    the shift (1 - 1/2tau) * 2 sigma F F / ((tau - 1/2) psi^2) that sets
+    Eq. 32's eps (the sigma term is what distinguishes Li et al.'s model)."""
+    for rho, u, F in random_states():
+        tau = RNG.uniform(0.6, 1.5)
+        psi = RNG.uniform(0.05, 0.4)
+        sigma = 0.105
+        f = orc.feq(rho, *u) * (1 + RNG.uniform(-0.05, 0.05, 9))
+        rho_f, j, _ = moments(f)
+        uf = j / rho_f
+        li = orc.collide_node(orc.params(4, 4, 0.7, tau, 0.0, 1.0, "bgk", "li", sigma=sigma), f, rho_f, *uf, *F, psi)
+        guo = orc.collide_node(orc.params(4, 4, 0.7, tau, 0.0, 1.0, "bgk", "guo"), f, rho_f, *uf, *F)
+        m0, m1, m2 = moments(li)
+        g0, g1, g2 = moments(guo)
+        assert m0 == pytest.approx(rho_f, rel=1e-14)
+        np.testing.assert_allclose(m1, j + F, rtol=1e-12, atol=1e-18)
+        shift = (1 - 1 / (2 * tau)) * 2 * sigma * np.outer(F, F) / ((tau - 0.5) * psi ** 2)
+        np.testing.assert_allclose(m2 - g2, shift, rtol=1e-6, atol=1e-16)   # a difference of O(0.1) moments
