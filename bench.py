@@ -481,7 +481,18 @@ def run_batch(args):
     with lbm.Batch(inst, collision="mrt") as b:
         nodes = b.nodes
         b.init()
-        ns, rows, carry, ms_tune = b.autotune(5)
+        cols, ns, rows, carry, ms_tune = b.autotune(5)
+        # each walk width at the chosen rows per item (host-timed, 20 steps)
+        by_cols = {}
+        for w, s_w, c_w in ((128, 3, False), (256, 3, True), (512, 2, True), (512, 3, True)):
+            b.set_tuning(w, s_w, rows, c_w)
+            b.step(3)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b.step(20)
+            torch.cuda.synchronize()
+            by_cols["%d/s%d%s" % (w, s_w, "c" if c_w else "")] = (time.perf_counter() - t0) / 20 * 1e3
+        b.set_tuning(cols, ns, rows, carry)
         b.step(args.warmup)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -503,8 +514,10 @@ def run_batch(args):
         "ms_per_step": t_step * 1e3,
         "roofline": {"bound": "hbm", "achieved": 72.0 * nodes / t_step / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": 72.0 * nodes / t_step / 1e9 / peak, "peak_kind": "%s (hbm_gbs, copy)" % peak_kind,
-                     "kernel": "k_step_batch (every instance running, host-timed over %d steps)" % args.batch_steps},
-        "tuning": {"stages": ns, "rows_per_item": rows, "carry": carry, "ms_per_step": ms_tune},
+                     "kernel": "%s (every instance running, host-timed over %d steps)"
+                               % ("k_step_batch" if cols == 128 else "k_step_batch_strip", args.batch_steps)},
+        "tuning": {"columns": cols, "stages": ns, "rows_per_item": rows, "carry": carry, "ms_per_step": ms_tune,
+                   "ms_per_step_by_columns": by_cols},
         "to_steady": {"wall_s": wall, "steps_done": done, "converged": int(conv.sum()),
                       "failed": int((state == lbm.FAILED).sum()), "running": int((state == lbm.RUNNING).sum()),
                       "median_steps": float(np.median(steps[conv])) if conv.any() else None,

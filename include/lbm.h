@@ -230,7 +230,7 @@ int lbm_autotune(lbm_ctx *ctx, int trial_steps, int *config, double *ms_per_step
  * Many independent periodic lattices with their own size, T/Tc, tau, A, K and
  * initial field (the paper's tau, T/Tc and EOS-scale sweeps, Secs. 4.2-4.4)
  * advanced together: one kernel launch per time step covers every running
- * instance through a table of (instance, 128-column strip, row chunk) work
+ * instance through a table of (instance, column strip, row chunk) work
  * items, each check interval is one CUDA graph, and convergence or failure is
  * decided per instance on the device.  Populations are FP32 deviations
  * (precision must be LBM_FP32_DEV; rho_ref = the instance's Maxwell vapour
@@ -331,15 +331,19 @@ int lbm_batch_read_density(lbm_batch *b, int i, double *rho_host);
  * past it repeat the farthest point rather than wrap onto the next image. */
 int lbm_batch_profiles(lbm_batch *b, int nb, const lbm_profile_geom *geom_host, double *prof_host);
 
-/* Tile shape of the batched step: row stages per warp, rows per work item,
- * and whether a row's pulled populations stay in registers from its psi pass
- * to its collision (carry = 1: stages 2 or 3, every stage in flight) or are
- * re-read from the stage (carry = 0: stages 3 or 4).  lbm_batch_autotune
- * times the candidates ((3, 0), (4, 0), (2, 1), (3, 1) x rows 32, 64, 128,
- * 256) for trial_steps steps each without advancing the state and keeps the
- * fastest; any output pointer may be NULL. */
-int lbm_batch_set_tuning(lbm_batch *b, int stages, int rows_per_item, int carry);
-int lbm_batch_autotune(lbm_batch *b, int trial_steps, int *stages, int *rows_per_item, int *carry,
+/* Tile shape of the batched step: the strip width of a work item, its row
+ * stages, rows per work item, and whether a row's pulled populations stay in
+ * registers from its psi pass to its collision (carry = 1: every stage in
+ * flight) or are re-read from the stage (carry = 0).
+ *   columns 128: one warp walks a strip; stages 3 or 4 (carry 0), 2 or 3 (carry 1).
+ *   columns 256: a 64-thread CTA walks a strip; stages 3, carry 1 only.
+ *   columns 512: a 128-thread CTA walks a strip; stages 2 or 3, carry 1 only.
+ * Other combinations return LBM_E_INVALID.  lbm_batch_autotune times the
+ * seven (columns, stages, carry) candidates x rows 32, 64, 128, 256 for trial_steps
+ * steps each without advancing the state and keeps the fastest; any output
+ * pointer may be NULL. */
+int lbm_batch_set_tuning(lbm_batch *b, int columns, int stages, int rows_per_item, int carry);
+int lbm_batch_autotune(lbm_batch *b, int trial_steps, int *columns, int *stages, int *rows_per_item, int *carry,
                        double *ms_per_step);
 
 /* Total lattice nodes of the batch (-1 if b is NULL). */

@@ -1,6 +1,7 @@
 // lbm_batch.cu -- many independent lattices stepped together: one launch per
-// time step covers every running instance through a table of warp work
-// items, check intervals are captured in CUDA graphs, and convergence and
+// time step covers every running instance through a table of work items
+// (one-warp walks of 128-column strips here, block-wide walks of wider
+// strips in lbm_batch_strip.cu), check intervals are captured in CUDA graphs, and convergence and
 // failure are decided per instance on the device.  Also the warm-start
 // helpers: radial density profiles of instances and initial fields built
 // from a profile, optionally with the populations at rest.
@@ -18,24 +19,12 @@
 #include <vector>
 
 #include "lbm.h"
+#include "lbm_batch.cuh"
 #include "lbm_host.h"
 #include "lbm_warp.cuh"
 
 namespace lbm {
 
-struct BInst {
-    long long off;        // population element offset (both buffers)
-    long long node_off;   // node offset of the FP64 per-node arrays
-    int nx, ny;
-    int tile_off;         // first observe tile (32 x 8) of this instance
-    int ntx, nty;
-    int kind;             // lbm_preset of the instance's geometry
-    int cell;
-    double size, width, rho_l, rho_v, noise_amp;
-    unsigned long long seed;
-    Coef<float> k;
-};
-struct BItem { int inst, x0, y0, y1, down, pad[3]; };   // down: walk the chunk's rows downwards
 struct BTile { int inst, tx, ty; };
 
 // Per-instance observables and convergence record (device).
@@ -48,7 +37,6 @@ struct BPart {
     double mx[5];         // max_v, max_dv, max_drho, rho_max, -rho_min
     unsigned status, pad;
 };
-enum : int { B_RUNNING = 0, B_CONVERGED = 1, B_FAILED = 2 };
 // Convergence snapshot per node in the compute type: v and the density
 // deviation drho (rho = rho_ref + drho).
 struct __align__(16) Snap { float vx, vy, drho, pad; };
@@ -510,7 +498,7 @@ struct lbm_batch {
     int* state = nullptr;        // device
     int* fail = nullptr;         // device
     unsigned* status = nullptr;  // device, per instance
-    int* queue = nullptr;        // device: the step's work-item counter and warps-done counter
+    int* queue = nullptr;        // device: the step's work-item counter and walkers-done counter
     BObs* obs = nullptr;         // device
     double2* probe_prev = nullptr;   // device: coexistence probes at the previous check
     // pinned host mirrors
@@ -520,6 +508,7 @@ struct lbm_batch {
     std::vector<long long> steps;
     long long total_steps = 0;
     // tuning
+    int cols = 128;              // strip width of a work item: 128 (one warp), 256 or 512 (a CTA)
     int ns = 3;                  // stages per warp (3 or 4; 2 or 3 with carry)
     int carry = 0;               // rows carried in registers from the psi pass to the collision
     int rows = 64;               // rows per work item
@@ -550,10 +539,8 @@ void drop_graphs(lbm_batch* b)
         if (g) { cudaGraphExecDestroy(g); g = nullptr; }
 }
 
-// Work items: every running instance, 128-column strips, chunks of about
-// b->rows rows (never under 8).
-// Work items of the running instances: 128-column strips cut into row chunks
-// of about b->rows rows.  When the running instances hold too few strip rows
+// Work items of the running instances: strips of b->cols columns cut into
+// row chunks of about b->rows rows.  When the running instances hold too few strip rows
 // to give every SM about sixteen items at that length (small batches, and
 // the tail of a run when a few instances remain), the chunks shrink -- down
 // to 16 rows -- so a step is spread over more warps (up to the 14-16 a
@@ -570,7 +557,7 @@ int build_items(lbm_batch* b, const int* host_state)
     for (int i = 0; i < b->n; ++i) {
         if (host_state && host_state[i] != B_RUNNING) continue;
         const BInst& I = b->hinst[i];
-        strip_rows += (long long)((I.nx + 127) / 128) * I.ny;
+        strip_rows += (long long)((I.nx + b->cols - 1) / b->cols) * I.ny;
     }
     const long long target = 16LL * nsm;
     const int rows = (int)std::max<long long>(std::min<long long>(b->rows, strip_rows / target), std::min(16, b->rows));
@@ -578,12 +565,12 @@ int build_items(lbm_batch* b, const int* host_state)
     for (int i = 0; i < b->n; ++i) {
         if (host_state && host_state[i] != B_RUNNING) continue;
         const BInst& I = b->hinst[i];
-        const int nstrips = (I.nx + 127) / 128;
+        const int nstrips = (I.nx + b->cols - 1) / b->cols;
         const int nch = std::max(1, (I.ny + rows / 2) / rows);
         for (int c = 0; c < nch; ++c) {
             const int y0 = int((long long)c * I.ny / nch), y1 = int((long long)(c + 1) * I.ny / nch);
             if (y1 <= y0) continue;
-            for (int s = 0; s < nstrips; ++s) it.push_back(BItem{i, s * 128, y0, y1, c & 1, {0, 0, 0}});
+            for (int s = 0; s < nstrips; ++s) it.push_back(BItem{i, s * b->cols, y0, y1, c & 1, {0, 0, 0}});
         }
     }
     // longest items first so the grid-stride loop ends evenly
@@ -634,10 +621,15 @@ int launch_batch_scheme(lbm_batch* b, const float* fin, float* fout)
     return launch_batch_step<BGK, SC, NS, CARRY>(b, fin, fout);
 }
 
-// The step with the batch's tuning: ns stages, rows carried in registers or
-// re-read from the stage ring.
+// The step with the batch's tuning: block-wide walks of wider strips, or
+// one-warp walks with ns stages, rows carried in registers or re-read from
+// the stage ring.
 int launch_batch_tuned(lbm_batch* b, const float* fin, float* fout)
 {
+    if (b->cols != 128)
+        return launch_batch_block(b->cols, b->ns, b->collision, b->forcing,
+                                  BatchLaunch{fin, fout, b->dinst, b->items, b->nitems, b->state, b->status, b->queue,
+                                              b->stream});
     if (b->carry) return b->ns == 3 ? launch_batch_scheme<3, true>(b, fin, fout)
                                     : launch_batch_scheme<2, true>(b, fin, fout);
     return b->ns == 4 ? launch_batch_scheme<4, false>(b, fin, fout) : launch_batch_scheme<3, false>(b, fin, fout);
@@ -1032,32 +1024,41 @@ int lbm_batch_profiles(lbm_batch* b, int nb, const lbm_profile_geom* geom_host, 
     return cuda_ok(e);
 }
 
-int lbm_batch_set_tuning(lbm_batch* b, int stages, int rows_per_item, int carry)
+int lbm_batch_set_tuning(lbm_batch* b, int columns, int stages, int rows_per_item, int carry)
 {
     if (!b || rows_per_item < 8) return LBM_E_INVALID;
-    if (carry ? (stages != 2 && stages != 3) : (stages != 3 && stages != 4)) return LBM_E_INVALID;
+    if (columns == 128) {
+        if (carry ? (stages != 2 && stages != 3) : (stages != 3 && stages != 4)) return LBM_E_INVALID;
+    } else if (!carry || !((columns == 256 && stages == 3) || (columns == 512 && (stages == 2 || stages == 3)))) {
+        return LBM_E_INVALID;
+    }
+    b->cols = columns;
     b->ns = stages;
     b->carry = carry ? 1 : 0;
     b->rows = rows_per_item;
     return build_items(b, b->h_state);
 }
 
-int lbm_batch_autotune(lbm_batch* b, int trial_steps, int* stages, int* rows_per_item, int* carry,
+int lbm_batch_autotune(lbm_batch* b, int trial_steps, int* columns, int* stages, int* rows_per_item, int* carry,
                        double* ms_per_step)
 {
     if (!b || trial_steps < 1) return LBM_E_INVALID;
     cudaEvent_t e0, e1;
     B_CUDA(cudaEventCreate(&e0));
     B_CUDA(cudaEventCreate(&e1));
-    const int cand_ns[4] = {3, 4, 2, 3};
-    const int cand_carry[4] = {0, 0, 1, 1};
+    // (columns, stages, carry): the one-warp walks, then the block walks
+    constexpr int ncand = 7;
+    const int cand_cols[ncand] = {128, 128, 128, 128, 256, 512, 512};
+    const int cand_ns[ncand] = {3, 4, 2, 3, 3, 2, 3};
+    const int cand_carry[ncand] = {0, 0, 1, 1, 1, 1, 1};
     const int cand_rows[4] = {32, 64, 128, 256};
     float best = 3.4e38f;
-    int bns = b->ns, brows = b->rows, bcarry = b->carry;
+    int bcols = b->cols, bns = b->ns, brows = b->rows, bcarry = b->carry;
     int status = LBM_OK;
     const int cur0 = b->cur;
-    for (int ci = 0; ci < 4 && status == LBM_OK; ++ci)
+    for (int ci = 0; ci < ncand && status == LBM_OK; ++ci)
         for (int ri = 0; ri < 4 && status == LBM_OK; ++ri) {
+            b->cols = cand_cols[ci];
             b->ns = cand_ns[ci];
             b->carry = cand_carry[ci];
             b->rows = cand_rows[ri];
@@ -1074,17 +1075,19 @@ int lbm_batch_autotune(lbm_batch* b, int trial_steps, int* stages, int* rows_per
             float ms = 0;
             cudaEventElapsedTime(&ms, e0, e1);
             ms /= trial_steps;
-            if (ms < best) { best = ms; bns = b->ns; brows = b->rows; bcarry = b->carry; }
+            if (ms < best) { best = ms; bcols = b->cols; bns = b->ns; brows = b->rows; bcarry = b->carry; }
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->cur = cur0;
+    b->cols = bcols;
     b->ns = bns;
     b->rows = brows;
     b->carry = bcarry;
     const int s = build_items(b, b->h_state);
     if (status != LBM_OK) return status;
     if (s != LBM_OK) return s;
+    if (columns) *columns = bcols;
     if (stages) *stages = bns;
     if (rows_per_item) *rows_per_item = brows;
     if (carry) *carry = bcarry;

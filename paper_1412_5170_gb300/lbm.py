@@ -122,8 +122,8 @@ _PROTOS = {
     "lbm_batch_results": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "lbm_batch_read_density": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "lbm_batch_profiles": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
-    "lbm_batch_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
-    "lbm_batch_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+    "lbm_batch_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "lbm_batch_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _dp]),
     "lbm_batch_nodes": (ctypes.c_int64, [_vp]),
     "lbm_ws_create": (ctypes.c_int, [ctypes.POINTER(lbm_ws_cfg), ctypes.POINTER(_vp)]),
@@ -422,15 +422,18 @@ class Batch:
         check(lbm_batch_profiles(self.h, int(nb), self._geom(geom), out.ctypes.data_as(_vp)), "lbm_batch_profiles")
         return out
 
-    def set_tuning(self, stages, rows, carry=False):
-        check(lbm_batch_set_tuning(self.h, int(stages), int(rows), int(bool(carry))), "lbm_batch_set_tuning")
+    def set_tuning(self, columns, stages, rows, carry=False):
+        """Strip width of a work item (128: one warp; 256, 512: a CTA), row
+        stages, rows per item, rows carried in registers."""
+        check(lbm_batch_set_tuning(self.h, int(columns), int(stages), int(rows), int(bool(carry))),
+              "lbm_batch_set_tuning")
 
     def autotune(self, trial_steps=10):
-        """Time the tile shapes; returns (stages, rows per item, carry, ms per step)."""
-        a, b, c, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
-        check(lbm_batch_autotune(self.h, int(trial_steps), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
-                                 ctypes.byref(ms)), "lbm_batch_autotune")
-        return a.value, b.value, bool(c.value), ms.value
+        """Time the tile shapes; returns (columns, stages, rows per item, carry, ms per step)."""
+        w, a, b, c, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        check(lbm_batch_autotune(self.h, int(trial_steps), ctypes.byref(w), ctypes.byref(a), ctypes.byref(b),
+                                 ctypes.byref(c), ctypes.byref(ms)), "lbm_batch_autotune")
+        return w.value, a.value, b.value, bool(c.value), ms.value
 
 
 def _f32(a, shape=None):

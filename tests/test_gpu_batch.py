@@ -189,11 +189,58 @@ def test_batch_autotune_keeps_state(lbm):
         b.init()
         b.step(5)
         before = [b.read_density(i) for i in range(len(inst))]
-        ns, rows, carry, ms = b.autotune(3)
-        assert (ns in (2, 3) if carry else ns in (3, 4)) and rows in (32, 64, 128, 256) and ms > 0
+        cols, ns, rows, carry, ms = b.autotune(3)
+        assert (cols, ns, carry) in {(128, 3, False), (128, 4, False), (128, 2, True), (128, 3, True),
+                                     (256, 3, True), (512, 2, True), (512, 3, True)}
+        assert rows in (32, 64, 128, 256) and ms > 0
         after = [b.read_density(i) for i in range(len(inst))]
     for x, y in zip(before, after):
         assert np.array_equal(x, y)
+
+
+def wide_instances():
+    """The batch instances plus a slab wider than a 512-column strip: ragged
+    last strips for both block walks (260 = 256 + 4, 520 = 512 + 8), and
+    instances narrower than a strip (64, 96, 132)."""
+    return instances() + [dict(nx=520, ny=24, kind="slab", T_over_Tc=0.8, tau=0.9, A=-0.304, K=0.7, size=6.0,
+                               seed=13)]
+
+
+@pytest.mark.parametrize("columns,stages", [(256, 3), (512, 2), (512, 3)])
+@pytest.mark.parametrize("coll,forc", [("mrt", "guo"), ("bgk", "guo"), ("bgk", "edm"), ("bgk", "sc")])
+def test_block_walks_match_warp_walk_and_oracle(lbm, columns, stages, coll, forc):
+    """The block-wide strip walks (a CTA per 256- or 512-column strip) give
+    the one-warp walk's fields, and both the oracle's, on 8-row items that
+    alternate their walk direction."""
+    inst = wide_instances()
+    steps = 60
+    out = {}
+    for w, s, c in ((128, 3, False), (columns, stages, True)):
+        with lbm.Batch(inst, collision=coll, forcing=forc) as b:
+            b.set_tuning(w, s, 8, c)
+            b.init()
+            b.step(steps)
+            out[w] = [b.read_density(i) for i in range(len(inst))]
+    for i, d in enumerate(inst):
+        assert np.abs(out[columns][i] - out[128][i]).max() < 1e-6 * out[128][i].max()
+        nx, ny = d.get("nx", d.get("side")), d.get("ny", d.get("side"))
+        rv, rl = lbm.maxwell(d["T_over_Tc"])
+        rho0 = synth.density_field(nx, ny, d["kind"], rl, rv, d["size"], seed=d["seed"])
+        q = oracle.params(nx, ny, d["T_over_Tc"], d["tau"], d["A"], d["K"], coll, forc, s_e=0.8, s_eps=0.8, s_q=1.1)
+        f, _ = oracle.run(q, oracle.init_rest(rho0), steps)
+        ref = f.sum(0)
+        assert (np.abs(out[columns][i] - ref) / ref).max() < 2e-5
+
+
+def test_batch_tuning_rejects_unknown_shapes(lbm):
+    with lbm.Batch(instances()[:1]) as b:
+        for bad in ((256, 2, 32, True), (256, 3, 32, False), (512, 4, 32, True), (512, 3, 32, False),
+                    (384, 3, 32, True),
+                    (128, 2, 32, False), (128, 3, 4, False)):
+            with pytest.raises(lbm.LbmError):
+                b.set_tuning(*bad)
+        b.set_tuning(512, 2, 32, True)
+        b.set_tuning(512, 3, 32, True)
 
 
 def test_batch_rejects_li_forcing(lbm):
