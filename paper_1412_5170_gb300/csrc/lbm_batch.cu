@@ -43,9 +43,6 @@ struct __align__(16) Snap { float vx, vy, drho, pad; };
 
 constexpr int kBatchWarps = 1;   // warps (independent 128-column walkers) per CTA
 
-// One time step of every running instance.  Each warp of a CTA walks work
-// items (instance, 128-column strip, row chunk) in a grid-stride loop; the
-// instance's constants are staged in shared memory per item.
 // Dynamic shared memory of one batched-step CTA: per warp its stage ring and
 // barriers (warp_smem), then one Coef per warp at a 16-byte aligned offset.
 // (No static shared memory: it would shift the dynamic region off the
@@ -573,7 +570,7 @@ int build_items(lbm_batch* b, const int* host_state)
             for (int s = 0; s < nstrips; ++s) it.push_back(BItem{i, s * b->cols, y0, y1, c & 1, {0, 0, 0}});
         }
     }
-    // longest items first so the grid-stride loop ends evenly
+    // longest items first, so the walkers taking them from the queue finish evenly
     std::stable_sort(it.begin(), it.end(), [](const BItem& a, const BItem& c) { return (a.y1 - a.y0) > (c.y1 - c.y0); });
     if ((int)it.size() > b->items_cap) {
         if (b->items) cudaFree(b->items);

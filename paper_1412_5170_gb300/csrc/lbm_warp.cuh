@@ -1,6 +1,7 @@
 // lbm_warp.cuh -- warp-per-strip fused step for FP32-deviation populations
-// (the throughput kernel): one warp owns a 128-column strip of a chunk of
-// rows and walks down it with no block-level barrier.
+// (the batched step's walk, and a candidate of the single-lattice autotuner):
+// one warp owns a 128-column strip of a chunk of rows and walks along it
+// with no block-level barrier.
 //
 // Per density row r the warp needs the pulled populations f*_a(x - e_a) on
 // row r plus one halo column each side.  Lanes 0..8 copy the nine source row
