@@ -136,6 +136,7 @@ _PROTOS = {
     "lbm_ws_train": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float,
                                     ctypes.c_uint64, ctypes.POINTER(ctypes.c_float)]),
     "lbm_ws_predict": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp]),
+    "lbm_stats_noalloc": (ctypes.c_int, [ctypes.POINTER(lbm_params), _vp, _vp, ctypes.POINTER(lbm_stats_t)]),
 }
 for _name, (_res, _args) in _PROTOS.items():
     _f = getattr(_lib, _name)

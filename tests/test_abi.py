@@ -33,6 +33,30 @@ def test_every_declared_symbol_is_exported(lib):
     assert not missing, missing
 
 
+def declared_prototypes():
+    """{name: number of parameters} of every function include/*.h declares."""
+    out = {}
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            for name, args in re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(lbm_[a-z_0-9]+)\s*\(([^;]*?)\)\s*;",
+                                         text, flags=re.M | re.S):
+                args = args.strip()
+                out[name] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_declares_every_function_with_its_arity(lbm):
+    """The Python binding carries the same names as the C ABI, each with as
+    many ctypes argument types as the header's prototype has parameters."""
+    protos = declared_prototypes()
+    assert set(protos) == set(declared_functions())
+    assert set(lbm._PROTOS) == set(protos)
+    wrong = {n: (k, len(lbm._PROTOS[n][1])) for n, k in protos.items() if len(lbm._PROTOS[n][1]) != k}
+    assert not wrong, wrong
+
+
 def test_strerror_and_version(lbm):
     assert lbm.lbm_strerror(0) == b"ok"
     assert b"converged" in lbm.lbm_strerror(lbm.E_NOT_CONVERGED)

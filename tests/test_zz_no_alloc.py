@@ -29,12 +29,8 @@ def stored_layout(f, rho_ref, dtype):
 
 
 def noalloc(lbm, params, buf, stream):
-    fn = lbm._lib.lbm_stats_noalloc
-    fn.restype = ctypes.c_int
-    fn.argtypes = [ctypes.POINTER(lbm.lbm_params), ctypes.c_void_p, ctypes.c_void_p,
-                   ctypes.POINTER(lbm.lbm_stats_t)]
     out = lbm.lbm_stats_t()
-    st = fn(ctypes.byref(params), ctypes.c_void_p(buf.data_ptr()), ctypes.c_void_p(stream.cuda_stream),
+    st = lbm.lbm_stats_noalloc(ctypes.byref(params), ctypes.c_void_p(buf.data_ptr()), ctypes.c_void_p(stream.cuda_stream),
             ctypes.byref(out))
     return st, out.as_dict()
 
