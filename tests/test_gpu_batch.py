@@ -69,11 +69,18 @@ def test_batch_against_oracle(lbm):
         assert (np.abs(got[i] - ref) / ref).max() < 2e-5
 
 
-def test_run_to_steady_isolates_failures_and_converges_the_rest(lbm):
+# the default one-warp walk, and the block walk of 512-column strips
+TUNINGS = [None, (512, 2, 16, True)]
+
+
+@pytest.mark.parametrize("tuning", TUNINGS)
+def test_run_to_steady_isolates_failures_and_converges_the_rest(lbm, tuning):
     inst = [dict(nx=8, ny=64, kind="slab", T_over_Tc=0.85, tau=1.0, A=-0.304, K=1.0, size=16.0, seed=5),
             dict(side=48, kind="droplet", T_over_Tc=0.5, tau=0.55, A=-0.152, K=1.0, size=12.0, seed=6),   # unstable
             dict(nx=12, ny=64, kind="slab", T_over_Tc=0.8, tau=0.9, A=-0.304, K=0.5, size=16.0, seed=7)]
     with lbm.Batch(inst) as b:
+        if tuning:
+            b.set_tuning(*tuning)
         b.init()
         st, done = b.run_to_steady(tol_rho=1e-6, check_every=500, max_steps=100000)
         state, code, steps, obs = b.results()
@@ -106,9 +113,13 @@ def test_coexistence_criterion_stops_when_probes_settle(lbm):
     assert obs["rho_row0"][1] == pytest.approx(ref["rho_row0"][1], rel=1e-3)
 
 
-def test_graph_intervals_equal_plain_steps(lbm):
+@pytest.mark.parametrize("tuning", TUNINGS)
+def test_graph_intervals_equal_plain_steps(lbm, tuning):
     inst = instances()
     with lbm.Batch(inst) as a, lbm.Batch(inst) as c:
+        if tuning:
+            a.set_tuning(*tuning)
+            c.set_tuning(*tuning)
         a.init()
         c.init()
         a.run_to_steady(tol_v=1e-30, check_every=50, max_steps=150)   # 3 graph-captured intervals
