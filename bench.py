@@ -742,7 +742,7 @@ def main():
     ap.add_argument("--ws-A", type=float, default=-0.84, help="Eq. 6 weight A of the sweep (epsilon = -2A = 1.68)")
     ap.add_argument("--ws-tol", type=float, default=1e-5, help="coexistence-density change per 1000 steps")
     ap.add_argument("--ws-max-steps", type=int, default=100000)
-    ap.add_argument("--cpu-steps", type=int, default=300,
+    ap.add_argument("--cpu-steps", type=int, default=700,
                     help="oracle steps on one 256x256 cell for cpu_baseline (0 = skip)")
     ap.add_argument("--size", type=int, default=4096, help="lattice side (multiple of 256; profiling)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false", help="skip the end-to-end leg")
