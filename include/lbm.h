@@ -189,6 +189,28 @@ int lbm_run_to_steady(lbm_ctx *ctx, double tol, int64_t check_every, int64_t max
  * each (any may be NULL).  v = u + F/(2 rho).  Synchronises. */
 int lbm_read_moments(lbm_ctx *ctx, double *rho_host, double *vx_host, double *vy_host);
 
+/* Asynchronous host I/O: the copies run on two copy streams of the context
+ * (one per direction) and overlap the steps queued around them.
+ *   lbm_init_density_async: as lbm_init_density; the copy of rho0_host into a
+ *     device staging array starts at once (after the previous asynchronous
+ *     init has read that array), and the init kernels follow it on the
+ *     context's stream.
+ *   lbm_read_moments_async: rho, vx, vy of the state reached by the work
+ *     queued so far (as lbm_read_moments) are written into one of two device
+ *     slots, alternately, and copied into the host buffers on the copy
+ *     stream.  A read into a slot whose previous copy is still in flight
+ *     waits for it on the device, not on the host.
+ *   lbm_wait_io: returns when every copy queued by these calls is done.
+ * Host buffers (ny*nx doubles each; page-locked, or the copies do not
+ * overlap) stay owned by the caller and must stay valid, and unread or
+ * unchanged, until lbm_wait_io returns.  The first call allocates the copy
+ * streams and 7*ny*nx device doubles (also for a context on a caller's
+ * workspace); lbm_destroy releases them.  None of the three synchronises
+ * the context's stream. */
+int lbm_init_density_async(lbm_ctx *ctx, const double *rho0_host);
+int lbm_read_moments_async(lbm_ctx *ctx, double *rho_host, double *vx_host, double *vy_host);
+int lbm_wait_io(lbm_ctx *ctx);
+
 /* Post-streaming populations f_a(x, t) (the distribution at the current time,
  * before collision) as 9*ny*nx doubles, and the inverse.  Synchronises. */
 int lbm_read_populations(lbm_ctx *ctx, double *f_host);

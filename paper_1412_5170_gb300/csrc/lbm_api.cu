@@ -34,6 +34,16 @@ struct lbm_ctx {
     DevStats* hstats;       // pinned host mirror
     int64_t steps;
     int config;             // 0 = generic kernel, k >= 1 = strip configuration k-1
+    // Asynchronous host I/O, set up by the first lbm_init_density_async or
+    // lbm_read_moments_async: one copy stream per direction, and device
+    // arrays io = [rho0 staging (n)][moment slot 0 (3n)][moment slot 1 (3n)].
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    double* io = nullptr;
+    cudaEvent_t ev_in_ready = nullptr;   // rho0 staged (s_in)
+    cudaEvent_t ev_in_free = nullptr;    // the init kernels have read the staging array (stream)
+    cudaEvent_t ev_mom[2] = {nullptr, nullptr};   // moments of slot k written (stream)
+    cudaEvent_t ev_out[2] = {nullptr, nullptr};   // slot k copied to the host (s_out)
+    int slot = 0;
 };
 
 namespace {
@@ -159,17 +169,53 @@ int step_once(lbm_ctx* c)
 }
 
 template <typename T, typename C>
-void launch_observe(lbm_ctx* c, int mode)
+void launch_observe(lbm_ctx* c, int mode, double* rho, double* vx, double* vy)
 {
     k_observe<T, C><<<generic_grid(c->p), GTX * GTY, 0, c->stream>>>(
-        (const T*)c->f[c->cur], c->p.nx, c->p.ny, make_coef<C>(c->p), mode, c->rho, c->vx, c->vy,
+        (const T*)c->f[c->cur], c->p.nx, c->p.ny, make_coef<C>(c->p), mode, rho, vx, vy,
         c->vsnap, c->parts, c->dstats, c->status);
+}
+
+// The moment fields (mode OBS_FIELDS) into the given device arrays.
+int observe_fields_into(lbm_ctx* c, double* rho, double* vx, double* vy)
+{
+    if (c->p.precision == LBM_FP64) launch_observe<double, double>(c, OBS_FIELDS, rho, vx, vy);
+    else launch_observe<float, float>(c, OBS_FIELDS, rho, vx, vy);
+    LBM_CUDA(cudaGetLastError());
+    return LBM_OK;
+}
+
+// The copy streams, events and device arrays of the asynchronous host I/O.
+int ensure_io(lbm_ctx* c)
+{
+    if (c->io) return LBM_OK;
+    // each piece is made once, so a call after a failed set-up completes it
+    const size_t n = (size_t)c->p.nx * c->p.ny;
+    if (!c->s_in) LBM_CUDA(cudaStreamCreateWithFlags(&c->s_in, cudaStreamNonBlocking));
+    if (!c->s_out) LBM_CUDA(cudaStreamCreateWithFlags(&c->s_out, cudaStreamNonBlocking));
+    cudaEvent_t* evs[6] = {&c->ev_in_ready, &c->ev_in_free, &c->ev_mom[0], &c->ev_mom[1], &c->ev_out[0], &c->ev_out[1]};
+    for (cudaEvent_t* e : evs)
+        if (!*e) LBM_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    LBM_CUDA(cudaMalloc(&c->io, 7 * n * sizeof(double)));
+    return LBM_OK;
+}
+
+void release_io(lbm_ctx* c)
+{
+    if (c->s_in) cudaStreamSynchronize(c->s_in);
+    if (c->s_out) cudaStreamSynchronize(c->s_out);
+    cudaEvent_t evs[6] = {c->ev_in_ready, c->ev_in_free, c->ev_mom[0], c->ev_mom[1], c->ev_out[0], c->ev_out[1]};
+    for (cudaEvent_t e : evs)
+        if (e) cudaEventDestroy(e);
+    if (c->s_in) cudaStreamDestroy(c->s_in);
+    if (c->s_out) cudaStreamDestroy(c->s_out);
+    if (c->io) cudaFree(c->io);
 }
 
 int observe(lbm_ctx* c, int mode)
 {
-    if (c->p.precision == LBM_FP64) launch_observe<double, double>(c, mode);
-    else launch_observe<float, float>(c, mode);
+    if (c->p.precision == LBM_FP64) launch_observe<double, double>(c, mode, c->rho, c->vx, c->vy);
+    else launch_observe<float, float>(c, mode, c->rho, c->vx, c->vy);
     LBM_CUDA(cudaGetLastError());
     if (mode & OBS_REDUCE) {
         k_reduce_final<<<1, 256, 0, c->stream>>>(c->parts, c->nparts, c->p.nx, c->dstats);
@@ -324,6 +370,7 @@ void lbm_destroy(lbm_ctx* c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    release_io(c);
     if (c->owns && c->ws) cudaFree(c->ws);
     if (c->hstats) cudaFreeHost(c->hstats);
     delete c;
@@ -345,6 +392,51 @@ int lbm_init_density(lbm_ctx* c, const double* rho0_host)
     const size_t n = (size_t)c->p.nx * c->p.ny;
     LBM_CUDA(cudaMemcpyAsync(c->rho, rho0_host, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     return lbm_init_density_dev(c, c->rho);
+}
+
+int lbm_init_density_async(lbm_ctx* c, const double* rho0_host)
+{
+    if (!c || !rho0_host) return LBM_E_INVALID;
+    int s = ensure_io(c);
+    if (s != LBM_OK) return s;
+    const size_t n = (size_t)c->p.nx * c->p.ny;
+    // the staging array is free once the previous asynchronous init has read it
+    LBM_CUDA(cudaStreamWaitEvent(c->s_in, c->ev_in_free, 0));
+    LBM_CUDA(cudaMemcpyAsync(c->io, rho0_host, n * sizeof(double), cudaMemcpyHostToDevice, c->s_in));
+    LBM_CUDA(cudaEventRecord(c->ev_in_ready, c->s_in));
+    LBM_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in_ready, 0));
+    if ((s = lbm_init_density_dev(c, c->io)) != LBM_OK) return s;
+    LBM_CUDA(cudaEventRecord(c->ev_in_free, c->stream));
+    return LBM_OK;
+}
+
+int lbm_read_moments_async(lbm_ctx* c, double* rho_host, double* vx_host, double* vy_host)
+{
+    if (!c) return LBM_E_INVALID;
+    int s = ensure_io(c);
+    if (s != LBM_OK) return s;
+    const size_t n = (size_t)c->p.nx * c->p.ny, nb = n * sizeof(double);
+    const int k = c->slot;
+    double* m = c->io + n + (size_t)k * 3 * n;
+    // the slot's arrays are free once its previous copies to the host are done
+    LBM_CUDA(cudaStreamWaitEvent(c->stream, c->ev_out[k], 0));
+    if ((s = observe_fields_into(c, m, m + n, m + 2 * n)) != LBM_OK) return s;
+    LBM_CUDA(cudaEventRecord(c->ev_mom[k], c->stream));
+    LBM_CUDA(cudaStreamWaitEvent(c->s_out, c->ev_mom[k], 0));
+    if (rho_host) LBM_CUDA(cudaMemcpyAsync(rho_host, m, nb, cudaMemcpyDeviceToHost, c->s_out));
+    if (vx_host) LBM_CUDA(cudaMemcpyAsync(vx_host, m + n, nb, cudaMemcpyDeviceToHost, c->s_out));
+    if (vy_host) LBM_CUDA(cudaMemcpyAsync(vy_host, m + 2 * n, nb, cudaMemcpyDeviceToHost, c->s_out));
+    LBM_CUDA(cudaEventRecord(c->ev_out[k], c->s_out));
+    c->slot = k ^ 1;
+    return LBM_OK;
+}
+
+int lbm_wait_io(lbm_ctx* c)
+{
+    if (!c) return LBM_E_INVALID;
+    if (c->s_in) LBM_CUDA(cudaStreamSynchronize(c->s_in));
+    if (c->s_out) LBM_CUDA(cudaStreamSynchronize(c->s_out));
+    return LBM_OK;
 }
 
 int lbm_init_preset(lbm_ctx* c, int kind, double size, double width, double rho_l, double rho_v,

@@ -98,6 +98,9 @@ _PROTOS = {
     "lbm_stats": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(lbm_stats_t)]),
     "lbm_run_to_steady": (ctypes.c_int, [_vp, ctypes.c_double, _i64, _i64, ctypes.POINTER(_i64)]),
     "lbm_read_moments": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lbm_init_density_async": (ctypes.c_int, [_vp, _vp]),
+    "lbm_read_moments_async": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lbm_wait_io": (ctypes.c_int, [_vp]),
     "lbm_read_populations": (ctypes.c_int, [_vp, _vp]),
     "lbm_write_populations": (ctypes.c_int, [_vp, _vp]),
     "lbm_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
@@ -211,6 +214,7 @@ class Lattice:
         check(lbm_create(ctypes.byref(params), _vp(self.stream.cuda_stream), _vp(ws_ptr) if ws_ptr else None,
                          nbytes.value, ctypes.byref(ctx)), "lbm_create")
         self.ctx = ctx
+        self._io_refs = []   # host arrays of asynchronous copies in flight
 
     @property
     def shape(self):
@@ -238,6 +242,32 @@ class Lattice:
         assert rho0.shape == self.shape
         check(lbm_init_density(self.ctx, _host_ptr(rho0)), "lbm_init_density")
         self.stream.synchronize()   # rho0 is pageable host memory owned by this call
+
+    def init_density_async(self, rho0: np.ndarray):
+        """As init_density, with the host-to-device copy on the context's copy
+        stream (no synchronisation).  rho0: C-contiguous float64 of the
+        lattice shape, page-locked for the copy to overlap; it is held until
+        wait_io and must not change before then."""
+        assert rho0.shape == self.shape
+        ptr = _host_ptr(rho0)
+        self._io_refs.append(rho0)
+        check(lbm_init_density_async(self.ctx, ptr), "lbm_init_density_async")
+
+    def read_moments_async(self, out):
+        """Queue a read of (rho, vx, vy) at the state reached by the work
+        queued so far into out (three C-contiguous float64 arrays of the
+        lattice shape, page-locked for overlap); they are filled once wait_io
+        returns."""
+        rho, vx, vy = out
+        assert rho.shape == vx.shape == vy.shape == self.shape
+        ptrs = [_host_ptr(a) for a in (rho, vx, vy)]
+        self._io_refs.append(out)
+        check(lbm_read_moments_async(self.ctx, *ptrs), "lbm_read_moments_async")
+
+    def wait_io(self):
+        """Wait for every asynchronous copy of this lattice."""
+        check(lbm_wait_io(self.ctx), "lbm_wait_io")
+        self._io_refs.clear()
 
     def init_density_dev(self, rho0_dev):
         check(lbm_init_density_dev(self.ctx, _vp(rho0_dev.data_ptr())), "lbm_init_density_dev")
