@@ -175,3 +175,40 @@ def test_li_closer_to_mechanical_solution_than_kupershtokh_at_low_temperature(or
     li = _slab(orc, 0.7, 0.0, 1.0, 1.0, "li", sigma=0.105)
     kup = _slab(orc, 0.7, -0.84, 1.0, 1.0, "guo")
     assert abs(li[1] - mech_g) < 0.2 * abs(kup[1] - mech_g)
+
+
+def test_droplets_follow_laplace_law(orc):
+    """Laplace's law on static droplets (64 x 64, R = 8, 12, 16, 20, T/Tc =
+    0.8, BGK + Guo, A = -0.304, tau = 1, K = 1, 8000 steps to rest): the jump
+    of the Eq. 30 pressure between the droplet's centre and the box corner
+    (bulk nodes, where the interaction pressure vanishes) lies on a straight
+    line through the origin in 1/R_eq, with R_eq = sqrt(excess mass /
+    (pi (rho_l - rho_v))) the radius the droplet settles at."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from oracle import coexistence as cx
+    n, tr, K, steps = 64, 0.8, 1.0, 8000
+    rg, rl, _ = cx.maxwell(tr)
+    T = tr * orc.Tc()
+    p = orc.params(n, n, tr, 1.0, -0.304, K, "bgk", "guo")
+
+    def settle(R):
+        f, st = orc.run(p, orc.init_rest(synth.density_field(n, n, "droplet", rl, rg, R, seed=1, noise_amp=0.0)),
+                        steps)
+        g, st2 = orc.run(p, f, 500)
+        return st, st2, f.sum(0), g.sum(0)
+
+    with ThreadPoolExecutor(4) as pool:   # the oracle's C calls release the GIL
+        runs = list(pool.map(settle, (8.0, 12.0, 16.0, 20.0)))
+    xs, ys = [], []
+    for st, st2, before, rho in runs:
+        assert st == 0 and st2 == 0
+        assert np.abs(rho - before).max() < 1e-9          # at rest: nothing moves over 500 more steps
+        r_in, r_out = rho[n // 2, n // 2], rho[0, 0]
+        xs.append(1.0 / np.sqrt(np.sum(rho - r_out) / (np.pi * (r_in - r_out))))
+        ys.append(orc.pressure(r_in, T, K) - orc.pressure(r_out, T, K))
+    slope, icpt = np.polyfit(xs, ys, 1)
+    fit = slope * np.array(xs) + icpt
+    assert slope > 0
+    assert np.max(np.abs(fit - ys)) < 0.01 * max(ys)      # a straight line in 1/R
+    assert abs(icpt) < 0.06 * max(ys)                     # through the origin
