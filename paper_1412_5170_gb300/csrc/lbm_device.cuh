@@ -212,12 +212,20 @@ __device__ __forceinline__ void collide(C g[9], C Fx, C Fy, const Coef<C>& k, C&
         g[7] = dg - (dx + dy) + b8;
         g[6] = dg - (dx - dy) - b8;
         g[8] = dg + (dx - dy) - b8;
+        // row 0 of M^-1 = M^T / n: f0 = m0/9 - 4 m_e/36 + 4 m_eps/36 (FP64;
+        // the FP32 path closes g[0] on the mass below)
+        if constexpr (sizeof(C) != sizeof(float)) g[0] = b0 - C(4) * b1 + C(4) * b2;
     }
-    // Every scheme conserves mass (sum f* = rho).  Close the rest population
-    // on it so that rounding in the equilibrium weights (4/9, 1/9, 1/36 and
-    // the 1/9 of M^-1 are inexact in binary) cannot bias the mass step after
-    // step; the residual is one unbiased rounding of g[0].
-    g[0] = drho - (((g[1] + g[3]) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8])));
+    // Every scheme conserves mass (sum f* = rho).  In FP32 the rest population
+    // is closed on it, so that rounding in the equilibrium weights (4/9, 1/9,
+    // 1/36 and the 1/9 of M^-1 are inexact in binary) cannot bias the mass
+    // step after step; the residual is one unbiased rounding of g[0].  In FP64
+    // that bias is about 1e-16 of the mass per step and g[0] keeps its own
+    // formula: closing it would conserve mass better than any FP64 evaluation
+    // of Eqs. 23 and 34 written out term by term, and drift from one by about
+    // 1e-15 of rho per step.
+    if constexpr (sizeof(C) == sizeof(float))
+        g[0] = drho - (((g[1] + g[3]) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8])));
 }
 
 // Status bits of a node after collision: non-finite output.

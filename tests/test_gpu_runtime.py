@@ -20,12 +20,24 @@ def lattice(lbm, nx=64, ny=48, precision="fp64", coll="mrt", tr=0.8, tau=0.9, A=
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
 def test_mass_is_conserved(lbm, precision, tol):
+    """FP32: the rest population is closed on the mass, so the FP64 mass sum
+    of the deviations drifts only by rounding.  FP64: each population keeps
+    its own formula, as in the oracle, whose weights (4/9, 1/9, 1/36) are
+    inexact in binary; the mass then drifts by a few 1e-14 per 1000 steps,
+    and the bar is 1e-13 or twice the oracle's own drift on the same run."""
     with lattice(lbm, precision=precision) as lat:
         lat.init_preset("droplet", 12.0, seed=1)
         m0 = lat.stats()["mass"]
         lat.step(1000)
         st = lat.stats()
     assert st["status"] == 0
+    if precision == "fp64":
+        rv, rl = lbm.maxwell(0.8)
+        rho0 = synth.density_field(64, 48, "droplet", rl, rv, 12.0, seed=1)
+        q = oracle.params(64, 48, 0.8, 0.9, -0.304, 1.0, "mrt", "guo", **MRT)
+        f, ost = oracle.run(q, oracle.init_rest(rho0), 1000)
+        assert ost == oracle.OK
+        tol = max(tol, 2 * abs(f.sum() - rho0.sum()) / rho0.sum())
     assert abs(st["mass"] - m0) / m0 < tol
 
 
