@@ -6,7 +6,9 @@
 #include <vector>
 
 #include "lbm.h"
-#ifdef __CUDACC__
+// LBM_HOST_ARITHMETIC: the per-node arithmetic compiled by a host compiler
+// (a test build, with __device__ and __forceinline__ defined beforehand)
+#if defined(__CUDACC__) || defined(LBM_HOST_ARITHMETIC)
 #include "lbm_device.cuh"
 #endif
 
@@ -30,7 +32,7 @@ int lbm_strip_config_count(int precision);
 StripConfig lbm_strip_config(int precision, int cfg);
 int lbm_strip_launch(const lbm_params* p, int cfg, const void* fin, void* fout, unsigned* status, cudaStream_t s);
 
-#ifdef __CUDACC__
+#if defined(__CUDACC__) || defined(LBM_HOST_ARITHMETIC)
 // Kernel constants of a parameter set in the compute type C.
 template <typename C>
 lbm::Coef<C> make_coef(const lbm_params& p)
@@ -57,4 +59,4 @@ lbm::Coef<C> make_coef(const lbm_params& p)
     }
     return k;
 }
-#endif  // __CUDACC__
+#endif  // __CUDACC__ || LBM_HOST_ARITHMETIC

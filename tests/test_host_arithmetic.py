@@ -1,0 +1,88 @@
+"""The library's per-node arithmetic (csrc/lbm_device.cuh with make_coef's
+kernel constants), compiled for the host by g++ and stepped by a plain FP64
+pull loop (tests/host_arithmetic/host_step.cpp), against the oracle on the
+CPU.  The GPU kernels run the same functions, so these tests catch a change
+of the FP64 arithmetic before any GPU run; the GPU parity tests hold the
+kernels themselves to the oracle."""
+import ctypes
+import os
+import shutil
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+
+from paper_1412_5170_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+EV = [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
+MRT = dict(s_e=0.8, s_eps=0.8, s_q=1.1)
+CUDA_INC = "/usr/local/cuda/include"
+
+
+@pytest.fixture(scope="module")
+def host(tmp_path_factory):
+    if not shutil.which("g++") or not os.path.exists(os.path.join(CUDA_INC, "cuda_runtime.h")):
+        pytest.skip("needs g++ and the CUDA headers")
+    from paper_1412_5170_gb300 import build
+    build.build()
+    libdir = os.path.dirname(build.LIB)
+    so = str(tmp_path_factory.mktemp("host_arithmetic") / "libhoststep.so")
+    subprocess.check_call(["g++", "-O2", "-ffp-contract=off", "-std=c++17", "-fPIC", "-shared",
+                           "-I", os.path.join(ROOT, "include"), "-I", os.path.join(ROOT, "paper_1412_5170_gb300", "csrc"),
+                           "-I", CUDA_INC, os.path.join(ROOT, "tests", "host_arithmetic", "host_step.cpp"),
+                           "-o", so, "-L", libdir, "-llbm", "-Wl,-rpath," + libdir])
+    lib = ctypes.CDLL(so)
+    from paper_1412_5170_gb300 import lbm
+    lib.host_run.argtypes = [ctypes.POINTER(lbm.lbm_params), ctypes.c_void_p, ctypes.c_int]
+    lib.host_run.restype = ctypes.c_int
+    return lib
+
+
+def stored(f):
+    """Library storage of the post-streaming populations f: s_a(x) = f_a(x + e_a)."""
+    return np.ascontiguousarray(np.stack([np.roll(f[a], (-ey, -ex), axis=(0, 1)) for a, (ex, ey) in enumerate(EV)]))
+
+
+def unstored(s):
+    return np.stack([np.roll(s[a], (ey, ex), axis=(0, 1)) for a, (ex, ey) in enumerate(EV)])
+
+
+def run_both(host, lbm, orc, nx, ny, tr, tau, A, K, coll, forc, steps, size, sigma=0.0, seed=3):
+    rv, rl = lbm.maxwell(tr)
+    rho0 = synth.density_field(nx, ny, "droplet", rl, rv, size, seed=seed)
+    p = lbm.make_params(nx, ny, tr, tau, A, K, coll, forc, "fp64", sigma=sigma, **MRT)
+    q = orc.params(nx, ny, tr, tau, A, K, coll, forc, sigma=sigma, **MRT)
+    f0 = orc.init_rest(rho0)
+    s = stored(f0)
+    with ThreadPoolExecutor(2) as pool:   # both C calls release the GIL
+        h = pool.submit(host.host_run, ctypes.byref(p), s.ctypes.data, steps)
+        o = pool.submit(orc.run, q, f0, steps)
+        st, (f, ost) = h.result(), o.result()
+    return st, ost, unstored(s), f, f0.sum()
+
+
+@pytest.mark.parametrize("coll,forc", [("bgk", "guo"), ("bgk", "edm"), ("bgk", "sc"), ("mrt", "guo"), ("bgk", "li")])
+def test_host_arithmetic_matches_oracle(host, lbm, orc, coll, forc):
+    """Every scheme, 300 steps of a droplet on a 40 x 24 lattice: all
+    populations within 1e-12 of the oracle's (relative to the largest)."""
+    A, sigma = (0.0, 0.105) if forc == "li" else (-0.304, 0.0)
+    st, ost, f, ref, _ = run_both(host, lbm, orc, 40, 24, 0.8, 0.9, A, 1.0, coll, forc, 300, 7.0, sigma=sigma)
+    assert st == 0 and ost == 0
+    assert np.abs(f - ref).max() / np.abs(ref).max() < 1e-12
+
+
+@pytest.mark.parametrize("coll,tr,tau", [("bgk", 0.7, 0.6), ("mrt", 0.6, 1.0)])
+def test_fp64_rest_population_follows_the_oracle_over_1000_steps(host, lbm, orc, coll, tr, tau):
+    """A sharp-interface droplet (128 x 128, R = 20, K = 1, A = -0.84), 1000
+    steps: max |drho|/rho < 1e-12, and the FP64 mass drifts as the oracle's
+    does.  Closing the FP64 rest population on the mass (as the FP32 step
+    does) conserves mass to 1e-16 but leaves the oracle by ~1.7e-15 per step,
+    about 1.7e-12 here."""
+    st, ost, f, ref, m0 = run_both(host, lbm, orc, 128, 128, tr, tau, -0.84, 1.0, coll, "guo", 1000, 20.0, seed=7)
+    assert st == 0 and ost == 0
+    rho, rref = f.sum(0), ref.sum(0)
+    assert (np.abs(rho - rref) / rref).max() < 1e-12
+    drift, odrift = abs(rho.sum() - m0) / m0, abs(rref.sum() - m0) / m0
+    assert drift < max(1e-13, 2 * odrift)
