@@ -222,6 +222,19 @@ int lbm_write_populations(lbm_ctx *ctx, const double *f_host);
 int lbm_save(lbm_ctx *ctx, const char *path);
 int lbm_load(lbm_ctx *ctx, const char *path);
 
+/* Failure detection of the staged kernels (no paper counterpart).  Every
+ * shared-memory stage wait of the strip kernels is bounded: a row copy that
+ * does not land within the poll limit makes the kernel flag a timeout, wait
+ * (again bounded) for the copies it has issued, and return, so that the
+ * context stays usable and lbm_stats / lbm_run_to_steady report
+ * LBM_E_TIMEOUT.  lbm_inject_stage_timeout makes that path run without a
+ * stuck copy: in the next time step only, the first stage wait of every CTA
+ * gives up at once.  The step then leaves its output undefined and latches
+ * LBM_E_TIMEOUT; re-initialise the state (lbm_init_*, lbm_load,
+ * lbm_write_populations) to go on.  LBM_E_UNSUPPORTED if the context runs
+ * the generic kernel (configuration 0), which stages nothing. */
+int lbm_inject_stage_timeout(lbm_ctx *ctx);
+
 /* Kernel variant in use: 0 = generic tiled kernel (any nx), 1 = pipelined
  * strip kernel (nx % 4 == 0).  lbm_set_variant forces one (1 selects the
  * first strip configuration; LBM_E_UNSUPPORTED if the lattice does not
@@ -435,8 +448,13 @@ int lbm_ws_predict(lbm_ws *w, const float *X_host, int n, float *Y_host);
  *     behind, so calls that overlap on the GPU (other threads or streams)
  *     race and must be serialised by the caller;
  *   - the first call on each device does a one-time set-up (it looks up the
- *     scratch array's device address with that device current); make that
- *     first call before any stream capture. */
+ *     scratch array's device address with that device current), and so does
+ *     the first call in each further CUDA context on it (the address belongs
+ *     to the context: after cudaDeviceReset, or in a context the caller
+ *     created, it is looked up again); make that first call before any
+ *     stream capture;
+ *   - each call waits for its stream (the result is read back into host
+ *     memory before it returns). */
 #define LBM_NOALLOC_MAX_TILES 65536
 int lbm_stats_noalloc(const lbm_params *p, const void *f_dev, void *cuda_stream, lbm_stats_t *out);
 

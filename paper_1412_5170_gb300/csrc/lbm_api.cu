@@ -29,11 +29,13 @@ struct lbm_ctx {
     bool have_snap;
     Partial* parts;
     int nparts;
+    unsigned* ticket;       // last-CTA counter of the strip observation (0 between launches)
     DevStats* dstats;
     unsigned* status;
     DevStats* hstats;       // pinned host mirror
     int64_t steps;
     int config;             // 0 = generic kernel, k >= 1 = strip configuration k-1
+    bool inject_timeout = false;   // the next step's first stage waits give up at once
     // Asynchronous host I/O, set up by the first lbm_init_density_async or
     // lbm_read_moments_async: one copy stream per direction, and device
     // arrays io = [rho0 staging (n)][moment slot 0 (3n)][moment slot 1 (3n)].
@@ -58,7 +60,7 @@ dim3 generic_grid(const lbm_params& p)
 }
 
 struct Layout {
-    size_t f0, f1, rho, vx, vy, vsnap, parts, dstats, status, total;
+    size_t f0, f1, rho, vx, vy, vsnap, parts, ticket, dstats, status, total;
 };
 
 Layout layout_of(const lbm_params& p)
@@ -74,6 +76,7 @@ Layout layout_of(const lbm_params& p)
     L.vy = o; o = align256(o + n * sizeof(double));
     L.vsnap = o; o = align256(o + n * sizeof(double2));
     L.parts = o; o = align256(o + (size_t)g.x * g.y * sizeof(Partial));
+    L.ticket = o; o = align256(o + sizeof(unsigned));
     L.dstats = o; o = align256(o + sizeof(DevStats));
     L.status = o; o = align256(o + sizeof(unsigned));
     L.total = o;
@@ -145,10 +148,10 @@ int default_config(const lbm_params& p)
 int n_configs(const lbm_params& p) { return 1 + (lbm_strip_supported(&p) ? lbm_strip_config_count(p.precision) : 0); }
 
 // One fused step from fin to fout with kernel configuration cfg.
-int launch_step(lbm_ctx* c, int cfg, const void* fin, void* fout)
+int launch_step(lbm_ctx* c, int cfg, const void* fin, void* fout, long long first_wait = kStageWaitPolls)
 {
     if (cfg >= 1) {
-        const int s = lbm_strip_launch(&c->p, cfg - 1, fin, fout, c->status, c->stream);
+        const int s = lbm_strip_launch(&c->p, cfg - 1, fin, fout, c->status, c->stream, first_wait);
         if (s != LBM_OK) return s;
     } else if (c->p.precision == LBM_FP64) {
         launch_generic_scheme<double, double>(c, fin, fout);
@@ -161,7 +164,9 @@ int launch_step(lbm_ctx* c, int cfg, const void* fin, void* fout)
 
 int step_once(lbm_ctx* c)
 {
-    const int s = launch_step(c, c->config, c->f[c->cur], c->f[c->cur ^ 1]);
+    const long long first_wait = c->inject_timeout ? 0 : kStageWaitPolls;
+    c->inject_timeout = false;
+    const int s = launch_step(c, c->config, c->f[c->cur], c->f[c->cur ^ 1], first_wait);
     if (s != LBM_OK) return s;
     c->cur ^= 1;
     c->steps += 1;
@@ -173,16 +178,31 @@ void launch_observe(lbm_ctx* c, int mode, double* rho, double* vx, double* vy)
 {
     k_observe<T, C><<<generic_grid(c->p), GTX * GTY, 0, c->stream>>>(
         (const T*)c->f[c->cur], c->p.nx, c->p.ny, make_coef<C>(c->p), mode, rho, vx, vy,
-        c->vsnap, c->parts, c->dstats, c->status);
+        reinterpret_cast<VSnap<C>*>(c->vsnap), c->parts, c->dstats, c->status);
+}
+
+// Observation of the current state: with the strip walk where the strip
+// kernel applies (one launch, reduction included), else the generic tiled
+// kernel followed (with OBS_REDUCE) by the one-CTA final reduction.
+int observe_into(lbm_ctx* c, int mode, double* rho, double* vx, double* vy)
+{
+    if (lbm_strip_supported(&c->p))
+        return observe_strip_launch(&c->p, c->f[c->cur], mode, rho, vx, vy, c->vsnap, c->parts, c->ticket,
+                                    c->dstats, c->status, c->stream);
+    if (c->p.precision == LBM_FP64) launch_observe<double, double>(c, mode, rho, vx, vy);
+    else launch_observe<float, float>(c, mode, rho, vx, vy);
+    LBM_CUDA(cudaGetLastError());
+    if (mode & OBS_REDUCE) {
+        k_reduce_final<<<1, 256, 0, c->stream>>>(c->parts, c->nparts, c->p.nx, c->dstats);
+        LBM_CUDA(cudaGetLastError());
+    }
+    return LBM_OK;
 }
 
 // The moment fields (mode OBS_FIELDS) into the given device arrays.
 int observe_fields_into(lbm_ctx* c, double* rho, double* vx, double* vy)
 {
-    if (c->p.precision == LBM_FP64) launch_observe<double, double>(c, OBS_FIELDS, rho, vx, vy);
-    else launch_observe<float, float>(c, OBS_FIELDS, rho, vx, vy);
-    LBM_CUDA(cudaGetLastError());
-    return LBM_OK;
+    return observe_into(c, OBS_FIELDS, rho, vx, vy);
 }
 
 // The copy streams, events and device arrays of the asynchronous host I/O.
@@ -212,17 +232,7 @@ void release_io(lbm_ctx* c)
     if (c->io) cudaFree(c->io);
 }
 
-int observe(lbm_ctx* c, int mode)
-{
-    if (c->p.precision == LBM_FP64) launch_observe<double, double>(c, mode, c->rho, c->vx, c->vy);
-    else launch_observe<float, float>(c, mode, c->rho, c->vx, c->vy);
-    LBM_CUDA(cudaGetLastError());
-    if (mode & OBS_REDUCE) {
-        k_reduce_final<<<1, 256, 0, c->stream>>>(c->parts, c->nparts, c->p.nx, c->dstats);
-        LBM_CUDA(cudaGetLastError());
-    }
-    return LBM_OK;
-}
+int observe(lbm_ctx* c, int mode) { return observe_into(c, mode, c->rho, c->vx, c->vy); }
 
 int status_code(unsigned bits)
 {
@@ -345,6 +355,7 @@ int lbm_create(const lbm_params* p, void* cuda_stream, void* workspace_dev, size
     c->vy = (double*)(b + L.vy);
     c->vsnap = (double2*)(b + L.vsnap);
     c->parts = (Partial*)(b + L.parts);
+    c->ticket = (unsigned*)(b + L.ticket);
     const dim3 g = generic_grid(*p);
     c->nparts = int(g.x * g.y);
     c->dstats = (DevStats*)(b + L.dstats);
@@ -602,6 +613,14 @@ int lbm_load(lbm_ctx* c, const char* path)
     const int s = reset_state(c);
     c->steps = h.steps;
     return s;
+}
+
+int lbm_inject_stage_timeout(lbm_ctx* c)
+{
+    if (!c) return LBM_E_INVALID;
+    if (c->config < 1) return LBM_E_UNSUPPORTED;   // the generic kernel has no staged copies
+    c->inject_timeout = true;
+    return LBM_OK;
 }
 
 int lbm_get_variant(lbm_ctx* c, int* variant)

@@ -58,7 +58,7 @@ k_step_batch_strip(const float* __restrict__ fin, float* __restrict__ fout, cons
         if (!run) continue;
         unsigned bad = 0;
         // the walk ends with a CTA barrier, after which sk and sit may be rewritten
-        const bool ok = strip_walk<float, float, COLL, FORC, NT, NS, CARRY, false, PSEAM>(
+        const bool ok = strip_walk_step<float, float, COLL, FORC, NT, NS, CARRY, false, PSEAM>(
             fin + I->off, fout + I->off, I->nx, I->ny, w.x0, w.y0, w.y1, w.down != 0, *sk, sm, G, bad);
         flag_status(bad, &inst_status[w.inst]);
         if (!ok) break;   // a stage wait timed out: the instance is flagged, stop this CTA

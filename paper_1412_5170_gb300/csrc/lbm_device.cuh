@@ -7,6 +7,7 @@
 // liquid's) keep their significant digits.  Every formula below is linear in
 // the w_a rho_ref shift, which therefore cancels exactly.
 #pragma once
+#include <cmath>
 #include <cstdint>
 
 namespace lbm {
@@ -30,6 +31,80 @@ __device__ __forceinline__ double cdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float csqrt(float a) { return a > 0.f ? a * rsqrtf(a) : 0.f; }
 __device__ __forceinline__ double csqrt(double a) { return sqrt(a); }
 
+// ---------------------------------------------------------------------------
+// FP32 arithmetic without biased constants.
+//
+// Near T/Tc = 0.5 with a small EOS scale K the vapour density of the model is
+// very sensitive to the effective temperature: a change of the pressure by
+// about 1e-8 rho moves rho_v by ~1e-4 of itself.  Float cannot hold 1/3, 1/12,
+// 1/6 (each rounds up by 3.0e-8 of itself) nor the D2Q9 weights 4/9, 1/9,
+// 1/36 (up by 7.45e-9), and a rounded constant scales the same term at every
+// node and every step by the same factor -- the force, the kinetic pressure
+// rho/3, the momentum source -- which is such a pressure change.  The FP32
+// step therefore applies every such constant either as an exact integer
+// (36 w_a = 16, 4, 1; the MRT row norms divide 36) or as an unevaluated sum
+// hi + lo of two floats (hi = float(c), lo = float(c - hi)) through one fused
+// multiply-add, and refines the hardware's approximate division and square
+// root by one Newton step.  What is left are roundings whose sign varies
+// from node to node.  Measured on the host copy of this arithmetic (64^2
+// droplet, T/Tc = 0.5, K = 1/16, 30 000 steps) the vapour density moves from
+// 1e-4 to a few 1e-6 of the FP64 oracle's.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float fma_rn(float a, float b, float c)
+{
+#ifdef __CUDA_ARCH__
+    return __fmaf_rn(a, b, c);
+#else
+    return std::fma(a, b, c);
+#endif
+}
+// a / b, 1 / b and sqrt(s) to about one ulp without the special-case
+// branches of the correctly rounded operations: the hardware approximation
+// followed by one Newton correction -- for the quotient q = a y (y ~ 1/b)
+// the residual r = a - b q, exact in one fused multiply-add, gives q + r y
+// (Markstein's correction); for the root r = s y (y ~ 1/sqrt(s)) Heron's
+// step r + (s - r^2) y/2.  The operands here are normal floats (densities in
+// (0, 1), their EOS terms, psi^2 > 0).  The host build (tests) uses the IEEE
+// operations.
+__device__ __forceinline__ float div_nr(float a, float b)
+{
+#ifdef __CUDA_ARCH__
+    const float y = __fdividef(1.0f, b);
+    const float q = a * y;
+    return fma_rn(fma_rn(-b, q, a), y, q);
+#else
+    return a / b;
+#endif
+}
+__device__ __forceinline__ float rcp_nr(float b)
+{
+#ifdef __CUDA_ARCH__
+    const float y = __fdividef(1.0f, b);
+    return fma_rn(fma_rn(-b, y, 1.0f), y, y);
+#else
+    return 1.0f / b;
+#endif
+}
+__device__ __forceinline__ float sqrt_nr(float s)   // s > 0
+{
+#ifdef __CUDA_ARCH__
+    const float y = rsqrtf(s);
+    const float r = s * y;
+    return fma_rn(fma_rn(-r, r, s), 0.5f * y, r);
+#else
+    return std::sqrt(s);
+#endif
+}
+// x c for a constant c = hi + lo held as two floats.
+__device__ __forceinline__ float mul_split(float x, float hi, float lo) { return fma_rn(x, hi, x * lo); }
+constexpr float kTwoThirdsHi = 0x1.555556p-1f, kTwoThirdsLo = -0x1.555556p-26f;   // 2/3
+constexpr float kTwelfthHi = 0x1.555556p-4f, kTwelfthLo = -0x1.555556p-29f;       // 1/12
+constexpr float k36thHi = 0x1.c71c72p-6f, k36thLo = -0x1.c71c72p-33f;             // 1/36
+constexpr float kNinthHi = 0x1.c71c72p-4f, kNinthLo = -0x1.c71c72p-31f;           // 1/9
+constexpr float kSixthHi = 0x1.555556p-3f, kSixthLo = -0x1.555556p-28f;           // 1/6
+// 36 w_a: the D2Q9 weights as exact integers.
+__host__ __device__ constexpr float w36(int a) { return a == 0 ? 16.f : (a < 5 ? 4.f : 1.f); }
+
 // Per-lattice constants in the compute type.
 template <typename C>
 struct Coef {
@@ -39,7 +114,7 @@ struct Coef {
     C one_m_A;    // 1 - A    (Eq. 6 effective-density term)
     C omega;      // 1/tau
     C tau;
-    C guo_pre;    // 1 - 1/(2 tau)  (Eq. 23)
+    C guo_pre;    // 1 - 1/(2 tau)  (Eq. 23); FP32: 1 - omega/2 exactly
     C s_e, s_eps, s_q;  // MRT rates (Eq. 35); s_nu = omega
     C rho_ref;    // deviation reference (0 for FP64)
     C li_c;       // sigma / (tau - 1/2): Li et al.'s v' = v + li_c F / psi^2 (Eq. 31)
@@ -47,7 +122,11 @@ struct Coef {
     // already divided by the squared norm n of its row of M (M^-1 = M^T / n):
     //   (m - s (m - m^eq) + (1 - s/2) S) / n = r0 m + r1 m^eq + r2 S
     // rows: 0 = e (s_e, n 36), 1 = eps (s_eps, 36), 2 = q (s_q, 12), 3 = nu (1/tau, 4)
+    // (FP64 path; the FP32 path relaxes with the rates themselves)
     C r0[4], r1[4], r2[4];
+    // FP32 path only (see "FP32 arithmetic without biased constants"):
+    C A;          // Eq. 6 weight
+    C tau_lo;     // tau + tau_lo = 1/omega (Shan-Chen shift: omega tau F = F exactly)
 };
 
 // psi from the K-scaled Carnahan-Starling EOS (Eqs. 29-30, a = 1, b = 4,
@@ -60,11 +139,22 @@ __device__ __forceinline__ C psi_of_rho(C rho, const Coef<C>& k, unsigned& bad)
     const C one_m = C(1) - eta;
     const C num = C(1) + eta * (C(1) + eta * (C(1) - eta));
     const C den = one_m * one_m * one_m;
-    const C p = k.K * (rho * k.T * cdiv(num, den) - rho * rho);
-    const C s = C(2) * (rho * (C(1) / C(3)) - p);
-    const bool ok = (rho > C(0)) && (rho < C(1)) && (s >= C(0));
-    if (!ok) bad |= ST_EOS;
-    return ok ? csqrt(s) : C(0);
+    if constexpr (sizeof(C) == sizeof(float)) {
+        // psi^2 = 2 rho/3 - 2 K rho (T q - rho), q the CS quotient: 2/3 as
+        // hi + lo, q Newton-refined, and T q - rho (a small difference in the
+        // liquid) in one fused multiply-add
+        const float q = div_nr(num, den);
+        const float s = fma_rn(-2.f * k.K * rho, fma_rn(k.T, q, -rho), mul_split(rho, kTwoThirdsHi, kTwoThirdsLo));
+        const bool ok = (rho > 0.f) && (rho < 1.f) && (s >= 0.f);
+        if (!ok) bad |= ST_EOS;
+        return (ok && s > 0.f) ? sqrt_nr(s) : 0.f;
+    } else {
+        const C p = k.K * (rho * k.T * cdiv(num, den) - rho * rho);
+        const C s = C(2) * (rho * (C(1) / C(3)) - p);
+        const bool ok = (rho > C(0)) && (rho < C(1)) && (s >= C(0));
+        if (!ok) bad |= ST_EOS;
+        return ok ? csqrt(s) : C(0);
+    }
 }
 
 // Kupershtokh's hybrid force (Eq. 6) with G = -1, U = -psi^2/2 and the
@@ -79,15 +169,31 @@ struct Stencil { C c, e, n, w, s, ne, nw, sw, se; };
 template <typename C>
 __device__ __forceinline__ void force(const Stencil<C>& q, const Coef<C>& k, C& Fx, C& Fy)
 {
-    const C w1 = C(1) / C(3), w2 = C(1) / C(12);
-    const C cc = k.one_m_A * q.c;
-    const C pe = q.e * (k.half_A * q.e + cc), pw = q.w * (k.half_A * q.w + cc);
-    const C pn = q.n * (k.half_A * q.n + cc), ps = q.s * (k.half_A * q.s + cc);
-    const C pne = q.ne * (k.half_A * q.ne + cc), psw = q.sw * (k.half_A * q.sw + cc);
-    const C pse = q.se * (k.half_A * q.se + cc), pnw = q.nw * (k.half_A * q.nw + cc);
-    const C d1 = pne - psw, d2 = pse - pnw;
-    Fx = w1 * (pe - pw) + w2 * (d1 + d2);
-    Fy = w1 * (pn - ps) + w2 * (d1 - d2);
+    if constexpr (sizeof(C) == sizeof(float)) {
+        // The same sum regrouped so that no rounded coefficient scales the
+        // leading term: F = psi(x) sum w psi(x+e) e + A sum w e psi(x+e)
+        // (psi(x+e)/2 - psi(x)), and per opposite pair (n, n')
+        //   phi(n) - phi(n') = (psi_n - psi_n') [psi(x) + A ((psi_n + psi_n')/2 - psi(x))],
+        // whose difference is exact and whose A term is of higher order;
+        // then F = (1/12) [4 (axis pair) + (diagonal pairs)].
+        const float c = q.c;
+        const float dx = (q.e - q.w) * fma_rn(k.A, 0.5f * (q.e + q.w) - c, c);
+        const float dy = (q.n - q.s) * fma_rn(k.A, 0.5f * (q.n + q.s) - c, c);
+        const float d1 = (q.ne - q.sw) * fma_rn(k.A, 0.5f * (q.ne + q.sw) - c, c);
+        const float d2 = (q.se - q.nw) * fma_rn(k.A, 0.5f * (q.se + q.nw) - c, c);
+        Fx = mul_split(4.f * dx + (d1 + d2), kTwelfthHi, kTwelfthLo);
+        Fy = mul_split(4.f * dy + (d1 - d2), kTwelfthHi, kTwelfthLo);
+    } else {
+        const C w1 = C(1) / C(3), w2 = C(1) / C(12);
+        const C cc = k.one_m_A * q.c;
+        const C pe = q.e * (k.half_A * q.e + cc), pw = q.w * (k.half_A * q.w + cc);
+        const C pn = q.n * (k.half_A * q.n + cc), ps = q.s * (k.half_A * q.s + cc);
+        const C pne = q.ne * (k.half_A * q.ne + cc), psw = q.sw * (k.half_A * q.sw + cc);
+        const C pse = q.se * (k.half_A * q.se + cc), pnw = q.nw * (k.half_A * q.nw + cc);
+        const C d1 = pne - psw, d2 = pse - pnw;
+        Fx = w1 * (pe - pw) + w2 * (d1 + d2);
+        Fy = w1 * (pn - ps) + w2 * (d1 - d2);
+    }
 }
 
 // Moments of the deviations (Eq. 3): drho = sum g (rho = rho_ref + drho),
@@ -109,11 +215,129 @@ __device__ __forceinline__ C feq_dev(int a, C drho, C rho, C ux, C uy, C usq15)
     return wt<C>(a) * (drho + rho * (C(3) * eu + C(4.5) * eu * eu - usq15));
 }
 
-// Collision of one node.  In: g (pulled deviations at time t), F, psi at the
-// node (used by Li et al.'s model only).  Out: g becomes the post-collision
-// deviations; vx, vy receive v = u + F/(2 rho).
+// FP32 collision, every scheme.  The D2Q9 weights enter as the integers
+// w36 = 36 w_a, and every product that carries a term of the size of rho
+// (the equilibria, Guo's and the exact-difference sources, the MRT moments of
+// rho, e, eps and j) is scaled by 1/36 (1/9, 1/6) held as hi + lo; the
+// momentum a step adds is then F exactly up to rounding (omega and
+// 1 - omega/2 are exact floats, see make_coef).  The moments, velocities and
+// relaxations are those of the FP64 collision below (same equations, same
+// readings); only the placement of the constants differs.  The reciprocal
+// 1/rho is Newton-refined: the exact-difference and Shan-Chen schemes take
+// their momentum source through it.
+template <int COLL, int FORC>
+__device__ __forceinline__ void collide_f32(float g[9], float Fx, float Fy, const Coef<float>& k, float& vx,
+                                            float& vy, float& rho_out, float psi)
+{
+    float drho, jx, jy;
+    moments(g, drho, jx, jy);
+    const float rho = k.rho_ref + drho;
+    const float inv_rho = rcp_nr(rho);
+    const float ux = jx * inv_rho, uy = jy * inv_rho;
+    vx = ux + 0.5f * Fx * inv_rho;
+    vy = uy + 0.5f * Fy * inv_rho;
+    rho_out = rho;
+    if constexpr (COLL == BGK && (FORC == GUO || FORC == LI)) {
+        // Eqs. 1, 2, 23 (Li et al.: Eq. 31, v' in the source's second-order
+        // term): omega f^eq + S = w36 (omega X + (1 - omega/2) Y) / 36, with
+        // X = (f^eq - w rho_ref)/w and Y = S / (w (1 - omega/2)); then
+        // f* = f + [(omega f^eq + S) - omega f], the bracket in one rounding.
+        float wx = vx, wy = vy;
+        if constexpr (FORC == LI) {
+            const float c = cdiv(k.li_c, psi * psi);
+            wx = vx + c * Fx;
+            wy = vy + c * Fy;
+        }
+        const float usq = 1.5f * (vx * vx + vy * vy);
+        const float wF3 = 3.f * (wx * Fx + wy * Fy);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            const float eF = float(ex(a)) * Fx + float(ey(a)) * Fy;
+            const float ev = float(ex(a)) * vx + float(ey(a)) * vy;
+            const float ew = float(ex(a)) * wx + float(ey(a)) * wy;
+            const float X = drho + rho * (3.f * ev + 4.5f * ev * ev - usq);
+            const float Y = 3.f * eF + 9.f * ew * eF - wF3;
+            const float Z = w36(a) * fma_rn(k.omega, X, k.guo_pre * Y);
+            g[a] = g[a] + fma_rn(-k.omega, g[a], mul_split(Z, k36thHi, k36thLo));
+        }
+    } else if constexpr (COLL == BGK && FORC == EDM) {
+        // Eqs. 1, 22: omega f^eq(u) + [f^eq(u + du) - f^eq(u)] = w36 (omega X + D) / 36
+        const float usq = 1.5f * (ux * ux + uy * uy);
+        const float dux = Fx * inv_rho, duy = Fy * inv_rho;
+        const float dq = 1.5f * (dux * (2.f * ux + dux) + duy * (2.f * uy + duy));
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            const float eu = float(ex(a)) * ux + float(ey(a)) * uy;
+            const float edu = float(ex(a)) * dux + float(ey(a)) * duy;
+            const float X = drho + rho * (3.f * eu + 4.5f * eu * eu - usq);
+            const float D = rho * (3.f * edu + 4.5f * edu * (2.f * eu + edu) - dq);
+            const float Z = w36(a) * fma_rn(k.omega, X, D);
+            g[a] = g[a] + fma_rn(-k.omega, g[a], mul_split(Z, k36thHi, k36thLo));
+        }
+    } else if constexpr (COLL == BGK && FORC == SC) {
+        // Eqs. 20-21, the shift tau F / rho with tau = 1/omega as hi + lo
+        const float tx = Fx * inv_rho, ty = Fy * inv_rho;
+        const float uex = ux + mul_split(tx, k.tau, k.tau_lo), uey = uy + mul_split(ty, k.tau, k.tau_lo);
+        const float usq = 1.5f * (uex * uex + uey * uey);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            const float eu = float(ex(a)) * uex + float(ey(a)) * uey;
+            const float X = w36(a) * (drho + rho * (3.f * eu + 4.5f * eu * eu - usq));
+            g[a] = g[a] + k.omega * (mul_split(X, k36thHi, k36thLo) - g[a]);
+        }
+    } else {
+        static_assert(COLL == MRT && FORC == GUO, "MRT supports Guo forcing only");
+        // Eq. 34 in the orthogonal basis (rho, e, eps, jx, qx, jy, qy, pxx,
+        // pxy): m* = m - s (m - m^eq) + (1 - s/2) S per moment, the conserved
+        // ones m0* = drho and j* = j + F (s_rho = s_j = 1), each divided by
+        // its row norm n (M^-1 = M^T / n).  The norms 9, 36 and 6 of the
+        // moments of the size of rho (rho, e, eps, j) are applied as hi + lo;
+        // q (n = 12) and the stresses (n = 4, exact) carry only velocity and
+        // force terms.
+        const float Sa = g[1] + g[3], Sb = g[2] + g[4], Sc = g[5] + g[7], Sd = g[6] + g[8];
+        const float axis = Sa + Sb, diag = Sc + Sd;
+        const float D1 = g[1] - g[3], D2 = g[2] - g[4], D57 = g[5] - g[7], D86 = g[8] - g[6];
+        const float m1 = 2.f * diag - axis - 4.f * g[0];
+        const float m2 = diag - 2.f * axis + 4.f * g[0];
+        const float m4 = (D57 + D86) - 2.f * D1;
+        const float m6 = (D57 - D86) - 2.f * D2;
+        const float m7 = Sa - Sb, m8 = Sc - Sd;
+        const float vx2 = vx * vx, vy2 = vy * vy;
+        const float rv2 = 3.f * rho * (vx2 + vy2);
+        const float vF6 = 6.f * (vx * Fx + vy * Fy);
+        const float se = k.s_e, sp = k.s_eps, sq = k.s_q, sn = k.omega;
+        const float b0 = mul_split(drho, kNinthHi, kNinthLo);
+        const float b1 = mul_split((m1 - se * (m1 - (rv2 - 2.f * drho))) + (1.f - 0.5f * se) * vF6,
+                                   k36thHi, k36thLo);
+        const float b2 = mul_split((m2 - sp * (m2 - (drho - rv2))) - (1.f - 0.5f * sp) * vF6,
+                                   k36thHi, k36thLo);
+        const float b3 = mul_split(jx + Fx, kSixthHi, kSixthLo), b5 = mul_split(jy + Fy, kSixthHi, kSixthLo);
+        const float b4 = ((m4 - sq * (m4 + rho * vx)) - (1.f - 0.5f * sq) * Fx) * (1.f / 12.f);
+        const float b6 = ((m6 - sq * (m6 + rho * vy)) - (1.f - 0.5f * sq) * Fy) * (1.f / 12.f);
+        const float b7 = 0.25f * ((m7 - sn * (m7 - rho * (vx2 - vy2))) + (1.f - 0.5f * sn) * (2.f * (vx * Fx - vy * Fy)));
+        const float b8 = 0.25f * ((m8 - sn * (m8 - rho * vx * vy)) + (1.f - 0.5f * sn) * (vx * Fy + vy * Fx));
+        const float ax = b0 - b1 - 2.f * b2;      // common part of e1..e4
+        const float dg = b0 + 2.f * b1 + b2;      // common part of e5..e8
+        const float px = b3 - 2.f * b4, py = b5 - 2.f * b6;
+        const float dx = b3 + b4, dy = b5 + b6;
+        g[1] = ax + px + b7;
+        g[3] = ax - px + b7;
+        g[2] = ax + py - b7;
+        g[4] = ax - py - b7;
+        g[5] = dg + (dx + dy) + b8;
+        g[7] = dg - (dx + dy) + b8;
+        g[6] = dg - (dx - dy) - b8;
+        g[8] = dg + (dx - dy) - b8;
+    }
+    // Every scheme conserves mass (sum f* = rho); the rest population is closed
+    // on it, so that no rounding can bias the mass step after step (the
+    // residual is one rounding of g[0] whose sign varies).
+    g[0] = drho - (((g[1] + g[3]) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8])));
+}
+
+// FP64 collision (the compute type C is double), every scheme.
 template <typename C, int COLL, int FORC>
-__device__ __forceinline__ void collide(C g[9], C Fx, C Fy, const Coef<C>& k, C& vx, C& vy, C& rho_out, C psi)
+__device__ __forceinline__ void collide_f64(C g[9], C Fx, C Fy, const Coef<C>& k, C& vx, C& vy, C& rho_out, C psi)
 {
     C drho, jx, jy;
     moments(g, drho, jx, jy);
@@ -212,20 +436,24 @@ __device__ __forceinline__ void collide(C g[9], C Fx, C Fy, const Coef<C>& k, C&
         g[7] = dg - (dx + dy) + b8;
         g[6] = dg - (dx - dy) - b8;
         g[8] = dg + (dx - dy) - b8;
-        // row 0 of M^-1 = M^T / n: f0 = m0/9 - 4 m_e/36 + 4 m_eps/36 (FP64;
-        // the FP32 path closes g[0] on the mass below)
-        if constexpr (sizeof(C) != sizeof(float)) g[0] = b0 - C(4) * b1 + C(4) * b2;
+        // row 0 of M^-1 = M^T / n: f0 = m0/9 - 4 m_e/36 + 4 m_eps/36
+        g[0] = b0 - C(4) * b1 + C(4) * b2;
     }
-    // Every scheme conserves mass (sum f* = rho).  In FP32 the rest population
-    // is closed on it, so that rounding in the equilibrium weights (4/9, 1/9,
-    // 1/36 and the 1/9 of M^-1 are inexact in binary) cannot bias the mass
-    // step after step; the residual is one unbiased rounding of g[0].  In FP64
-    // that bias is about 1e-16 of the mass per step and g[0] keeps its own
-    // formula: closing it would conserve mass better than any FP64 evaluation
-    // of Eqs. 23 and 34 written out term by term, and drift from one by about
-    // 1e-15 of rho per step.
-    if constexpr (sizeof(C) == sizeof(float))
-        g[0] = drho - (((g[1] + g[3]) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8])));
+    // The rest population keeps its own formula here (the FP32 collision
+    // closes it on the mass instead): in FP64 the weights' rounding biases the
+    // mass by about 1e-16 per step, and closing g[0] would conserve mass better
+    // than any FP64 evaluation of Eqs. 23 and 34 written out term by term,
+    // drifting from one by about 1e-15 of rho per step.
+}
+
+// Collision of one node.  In: g (pulled deviations at time t), F, psi at the
+// node (used by Li et al.'s model only).  Out: g becomes the post-collision
+// deviations; vx, vy receive v = u + F/(2 rho).
+template <typename C, int COLL, int FORC>
+__device__ __forceinline__ void collide(C g[9], C Fx, C Fy, const Coef<C>& k, C& vx, C& vy, C& rho_out, C psi)
+{
+    if constexpr (sizeof(C) == sizeof(float)) collide_f32<COLL, FORC>(g, Fx, Fy, k, vx, vy, rho_out, psi);
+    else collide_f64<C, COLL, FORC>(g, Fx, Fy, k, vx, vy, rho_out, psi);
 }
 
 // Status bits of a node after collision: non-finite output.

@@ -7,6 +7,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include "lbm.h"
 #include "lbm_device.cuh"
 
 namespace lbm {
@@ -111,6 +112,34 @@ k_step_generic(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, 
 // ---------------------------------------------------------------------------
 enum : int { OBS_FIELDS = 1, OBS_REDUCE = 2, OBS_SNAP_CMP = 4, OBS_SNAP_STORE = 8 };
 
+// Velocity snapshot of one node in the compute type (v is computed in it, so
+// a float snapshot of the FP32 path loses nothing).
+template <typename C> struct VSnapOf;
+template <> struct VSnapOf<float> { using type = float2; };
+template <> struct VSnapOf<double> { using type = double2; };
+template <typename C> using VSnap = typename VSnapOf<C>::type;
+__device__ __forceinline__ float2 make_vsnap(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ double2 make_vsnap(double x, double y) { return make_double2(x, y); }
+
+// rho - rho_ref and v = u + F/(2 rho) of one node from its pulled deviations
+// (Eq. 3 and Sec. 3.2), as every observation computes them (FP32: the
+// reciprocal Newton-refined).
+template <typename C>
+__device__ __forceinline__ void node_velocity(const C g[9], C Fx, C Fy, const Coef<C>& k, C& drho, C& vx, C& vy)
+{
+    C jx, jy;
+    moments<C>(g, drho, jx, jy);
+    const C rc = k.rho_ref + drho;
+    if constexpr (sizeof(C) == sizeof(float)) {
+        const float inv = rcp_nr(rc);
+        vx = fma_rn(0.5f * Fx, inv, jx * inv);
+        vy = fma_rn(0.5f * Fy, inv, jy * inv);
+    } else {
+        vx = jx / rc + C(0.5) * Fx / rc;
+        vy = jy / rc + C(0.5) * Fy / rc;
+    }
+}
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -144,7 +173,7 @@ template <typename T, typename C>
 __global__ void __launch_bounds__(GTX * GTY)
 k_observe(const T* __restrict__ fin, int nx, int ny, Coef<C> k, int mode,
           double* __restrict__ rho_o, double* __restrict__ vx_o, double* __restrict__ vy_o,
-          double2* __restrict__ vsnap, Partial* __restrict__ parts, DevStats* __restrict__ ds,
+          VSnap<C>* __restrict__ vsnap, Partial* __restrict__ parts, DevStats* __restrict__ ds,
           const unsigned* __restrict__ status)
 {
     __shared__ C sp[(GTY + 2) * (GTX + 2)];
@@ -170,13 +199,10 @@ k_observe(const T* __restrict__ fin, int nx, int ny, Coef<C> k, int mode,
         const int W = GTX + 2, c = (ty + 1) * W + tx + 1;
         Stencil<C> q{sp[c], sp[c + 1], sp[c + W], sp[c - 1], sp[c - W],
                      sp[c + W + 1], sp[c + W - 1], sp[c - W - 1], sp[c - W + 1]};
-        C Fx, Fy, drho, jx, jy;
+        C Fx, Fy, drho, vx, vy;
         force<C>(q, k, Fx, Fy);
-        moments<C>(g, drho, jx, jy);
+        node_velocity<C>(g, Fx, Fy, k, drho, vx, vy);
         rho = double(k.rho_ref) + double(drho);
-        const C rc = k.rho_ref + drho;
-        const C vx = jx / rc + C(0.5) * Fx / rc;
-        const C vy = jy / rc + C(0.5) * Fy / rc;
         if (!isfinite(drho) || !isfinite(vx) || !isfinite(vy)) bad |= ST_NONFINITE;
         const size_t o = (size_t)y * nx + x;
         if (mode & OBS_FIELDS) {
@@ -185,12 +211,12 @@ k_observe(const T* __restrict__ fin, int nx, int ny, Coef<C> k, int mode,
             if (vy_o) vy_o[o] = double(vy);
         }
         if (mode & OBS_SNAP_CMP) {
-            const double2 s = vsnap[o];
+            const VSnap<C> s = vsnap[o];
             const C dx = vx - C(s.x), dy = vy - C(s.y);
             mdv = sqrt(dx * dx + dy * dy);
             if (isnan(mdv)) mdv = obs_huge<C>();
         }
-        if (mode & OBS_SNAP_STORE) vsnap[o] = make_double2(double(vx), double(vy));
+        if (mode & OBS_SNAP_STORE) vsnap[o] = make_vsnap(vx, vy);
         mass = rho;
         mv = sqrt(vx * vx + vy * vy);
         if (isnan(mv)) mv = obs_huge<C>();
@@ -337,5 +363,15 @@ __global__ void k_plane_convert(T* __restrict__ fs, double* __restrict__ plane, 
         }
     }
 }
+
+// The observation with the strip walk (lbm_observe.cu), for lattices the strip
+// kernel supports (nx % 4 == 0): mode as k_observe; with OBS_REDUCE the per-CTA
+// partials (parts, at least as many as the generic observation's tiles) are
+// reduced in the same launch by the last CTA to finish, in a fixed order,
+// into ds (ticket: a device counter that is 0 between launches).  vsnap holds
+// VSnap<C> of the precision's compute type.
+int observe_strip_launch(const lbm_params* p, const void* f, int mode, double* rho, double* vx, double* vy,
+                         void* vsnap, Partial* parts, unsigned* ticket, DevStats* ds, const unsigned* status,
+                         cudaStream_t s);
 
 }  // namespace lbm

@@ -13,6 +13,8 @@
 // until the process exits.  Its size caps the lattice: at most
 // LBM_NOALLOC_MAX_TILES tiles of 32 x 8 nodes (any lattice up to
 // 4096 x 4096 fits).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -35,25 +37,67 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-void* g_scratch_dev[kMaxDevices] = {};   // device address of the scratch, per device
+// Device address of the scratch per device, with the CUDA context it was
+// looked up in: each context loads its own copy of the library's device code,
+// so the address is only valid in that context.
+struct ScratchAddr {
+    unsigned long long ctx_id;   // 0: no entry
+    void* ptr;
+};
+ScratchAddr g_scratch[kMaxDevices] = {};
 
-// Set-up, once per device with that device current: look up the device
-// address of the scratch array.
+// ID of the CUDA context current on this thread (0 if none or unknown).  The
+// driver gives every context an ID that is never reused in the process, so a
+// context destroyed and created again (cudaDeviceReset, a caller's own
+// cuCtxCreate) never matches an old entry.  The two driver calls are reached
+// through the runtime's entry-point query, so the library needs no link to
+// the driver library.
+unsigned long long current_context_id()
+{
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(f);
+    });
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Set-up, once per device and CUDA context, with that device current: look up
+// the device address of the scratch array in the current context.  A call
+// made in another context than the cached entry's (or where the context ID
+// cannot be read) looks the address up again.
 int scratch_address(void** out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBM_E_CUDA;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_dev[dev]) {
-        void* ptr = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess || !ptr) {
-            std::fprintf(stderr, "liblbm: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
-            return LBM_E_CUDA;
-        }
-        g_scratch_dev[dev] = ptr;
+    unsigned long long id = current_context_id();
+    if (id != 0 && g_scratch[dev].ctx_id == id) {
+        *out = g_scratch[dev].ptr;
+        return LBM_OK;
     }
-    *out = g_scratch_dev[dev];
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) {
+        std::fprintf(stderr, "liblbm: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
+        return LBM_E_CUDA;
+    }
+    if (id == 0) id = current_context_id();   // the look-up made the runtime's context current
+    g_scratch[dev] = ScratchAddr{id, ptr};
+    *out = ptr;
     return LBM_OK;
 }
 
@@ -72,7 +116,7 @@ extern "C" int lbm_stats_noalloc(const lbm_params* p, const void* f_dev, void* c
     if (!p || !f_dev || !out) return LBM_E_INVALID;
     const int v = lbm_validate_params(p);
     if (v != LBM_OK) return v;
-    const long long tiles = (long long)((p->nx + GTX - 1) / GTX) * ((p->ny + GTY - 1) / GTY);
+    const long long tiles = (((long long)p->nx + GTX - 1) / GTX) * (((long long)p->ny + GTY - 1) / GTY);
     if (tiles > LBM_NOALLOC_MAX_TILES) {
         std::fprintf(stderr, "liblbm: lbm_stats_noalloc: %d x %d lattice needs %lld tiles, more than the "
                      "fixed scratch holds (%d)\n", p->nx, p->ny, tiles, LBM_NOALLOC_MAX_TILES);

@@ -6,8 +6,10 @@ extern const StripConfig kStripF32[];
 extern const int kStripF32Count;
 extern const StripConfig kStripF64[];
 extern const int kStripF64Count;
-int lbm_strip_launch_f32(const lbm_params* p, int cfg, const void* fin, void* fout, unsigned* st, cudaStream_t s);
-int lbm_strip_launch_f64(const lbm_params* p, int cfg, const void* fin, void* fout, unsigned* st, cudaStream_t s);
+int lbm_strip_launch_f32(const lbm_params* p, int cfg, const void* fin, void* fout, unsigned* st, cudaStream_t s,
+                         long long first_wait);
+int lbm_strip_launch_f64(const lbm_params* p, int cfg, const void* fin, void* fout, unsigned* st, cudaStream_t s,
+                         long long first_wait);
 
 bool lbm_strip_supported(const lbm_params* p)
 {
@@ -26,9 +28,10 @@ StripConfig lbm_strip_config(int precision, int cfg)
     return precision == LBM_FP64 ? kStripF64[cfg] : kStripF32[cfg];
 }
 
-int lbm_strip_launch(const lbm_params* p, int cfg, const void* fin, void* fout, unsigned* status, cudaStream_t s)
+int lbm_strip_launch(const lbm_params* p, int cfg, const void* fin, void* fout, unsigned* status, cudaStream_t s,
+                     long long first_wait)
 {
     if (!lbm_strip_supported(p)) return LBM_E_UNSUPPORTED;
-    if (p->precision == LBM_FP64) return lbm_strip_launch_f64(p, cfg, fin, fout, status, s);
-    return lbm_strip_launch_f32(p, cfg, fin, fout, status, s);
+    if (p->precision == LBM_FP64) return lbm_strip_launch_f64(p, cfg, fin, fout, status, s, first_wait);
+    return lbm_strip_launch_f32(p, cfg, fin, fout, status, s, first_wait);
 }

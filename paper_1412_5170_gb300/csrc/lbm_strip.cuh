@@ -33,7 +33,7 @@
 
 namespace lbm {
 
-constexpr long long kWaitLimit = 1ll << 26;   // try_wait polls before a stage is declared stuck
+constexpr long long kWaitLimit = kStageWaitPolls;   // try_wait polls before a stage is declared stuck
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -58,10 +58,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
     return ok != 0;
 }
 
-// Bounded wait on one phase of an mbarrier; false if it did not complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity)
+// Bounded wait on one phase of an mbarrier (at most limit polls); false if
+// it did not complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long limit = kWaitLimit)
 {
-    for (long long i = 0; i < kWaitLimit; ++i)
+    for (long long i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -216,6 +217,42 @@ __device__ __forceinline__ void strip_init_barriers(const StripSmem<T, C, NT, NS
     __syncthreads();
 }
 
+// What a strip walk does with each chunk row once its psi neighbours are in
+// the ring: called by every thread with the density row y, the lane's first
+// column x (nodes x .. x+3, valid where active), its pulled deviations g, and
+// psi at columns x-1 .. x+4 of rows y-1 (rm), y (r0) and y+1 (rp).
+//
+// StepRow, the time step: Eq. 6 force, the collision, and nine 128-bit
+// stores of the post-collision deviations.
+template <typename T, typename C, int COLL, int FORC>
+struct StepRow {
+    T* __restrict__ fout;
+    int nx;
+    size_t n;
+    __device__ __forceinline__ void operator()(int y, int x, bool active, C (&gc)[9][4], const C (&rm)[6],
+                                               const C (&r0)[6], const C (&rp)[6], const Coef<C>& k,
+                                               unsigned& bad) const
+    {
+        if (!active) return;
+        T o[9][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            Stencil<C> q{r0[j + 1], r0[j + 2], rp[j + 1], r0[j], rm[j + 1], rp[j + 2], rp[j], rm[j], rm[j + 2]};
+            C Fx, Fy, vx, vy, rho, gj[9];
+            force<C>(q, k, Fx, Fy);
+#pragma unroll
+            for (int a = 0; a < 9; ++a) gj[a] = gc[a][j];
+            collide<C, COLL, FORC>(gj, Fx, Fy, k, vx, vy, rho, q.c);
+            if (!isfinite(gj[0])) bad |= ST_NONFINITE;   // g0 depends on all the others
+#pragma unroll
+            for (int a = 0; a < 9; ++a) o[a][j] = T(gj[a]);
+        }
+        T* out = fout + (size_t)y * nx + x;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) stg4(out + a * n, o[a][0], o[a][1], o[a][2], o[a][3]);
+    }
+};
+
 // Walk one strip segment: columns [x0, x0 + min(W, nx - x0)), rows [y0, y1).
 // G counts walk rows over every segment this CTA has walked: row G uses
 // stage G % NS in its (G / NS)-th phase, so segments can follow one another
@@ -229,11 +266,11 @@ __device__ __forceinline__ void strip_init_barriers(const StripSmem<T, C, NT, NS
 // y1 - kr instead of y0 - 1 + kr; the psi rows y - 1 and y + 1 of the
 // stencil swap ring slots).  All threads of the CTA call this with the same
 // arguments.
-template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY, bool HALO1 = false,
-          bool PSEAM = false>
-__device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny,
-                                           int x0, int y0, int y1, bool down, const Coef<C>& k,
-                                           const StripSmem<T, C, NT, NS>& sm, unsigned& G, unsigned& bad)
+template <typename T, typename C, int NT, int NS, bool CARRY, bool HALO1, bool PSEAM, class Row>
+__device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, int nx, int ny, int x0, int y0, int y1,
+                                           bool down, const Coef<C>& k, const StripSmem<T, C, NT, NS>& sm,
+                                           unsigned& G, unsigned& bad, Row& row,
+                                           long long first_wait = kWaitLimit)
 {
     using SM = StripSmem<T, C, NT, NS>;
     constexpr int SW = SM::SW, PW = SM::PW;
@@ -300,7 +337,7 @@ __device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restr
     auto body = [&](int kk, C (&gn)[9][4], C (&gc)[9][4]) -> bool {
         const unsigned g = base + kk;
         const T* st = sm.stages + (g % NS) * 9 * SW;
-        const bool ok = mbar_wait(&sm.bars[g % NS], (g / NS) & 1);
+        const bool ok = mbar_wait(&sm.bars[g % NS], (g / NS) & 1, kk == 0 ? first_wait : kWaitLimit);
         C* prow = sm.psi + (kk & 3) * PW;
         if (ok) {
             pull4_shfl<T, C>(st, SW, c0, lsm, rsm, gn);
@@ -334,26 +371,7 @@ __device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restr
             psi_row6<C>(sm.psi + ((down ? kc + 1 : kc - 1) & 3) * PW, c0, lsm, rsm, rm);
             psi_row6<C>(sm.psi + (kc & 3) * PW, c0, lsm, rsm, r0);
             psi_row6<C>(sm.psi + ((down ? kc - 1 : kc + 1) & 3) * PW, c0, lsm, rsm, rp);
-            if (active) {
-                T o[9][4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    Stencil<C> q{r0[j + 1], r0[j + 2], rp[j + 1], r0[j], rm[j + 1],
-                                 rp[j + 2], rp[j], rm[j], rm[j + 2]};
-                    C Fx, Fy, vx, vy, rho, gj[9];
-                    force<C>(q, k, Fx, Fy);
-#pragma unroll
-                    for (int a = 0; a < 9; ++a) gj[a] = gc[a][j];
-                    collide<C, COLL, FORC>(gj, Fx, Fy, k, vx, vy, rho, q.c);
-                    if (!isfinite(gj[0])) bad |= ST_NONFINITE;   // g0 closes on all others
-#pragma unroll
-                    for (int a = 0; a < 9; ++a) o[a][j] = T(gj[a]);
-                }
-                const int y = down ? y1 - kc : y0 + kc - 1;
-                T* out = fout + (size_t)y * nx + x0 + c0;
-#pragma unroll
-                for (int a = 0; a < 9; ++a) stg4(out + a * n, o[a][0], o[a][1], o[a][2], o[a][3]);
-            }
+            row(down ? y1 - kc : y0 + kc - 1, x0 + c0, active, gc, rm, r0, rp, k, bad);
         }
         return true;
     };
@@ -376,12 +394,25 @@ __device__ __forceinline__ bool strip_walk(const T* __restrict__ fin, T* __restr
     return true;
 }
 
+// A strip walk of the time step (StepRow) from fin into fout.
+template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY, bool HALO1 = false,
+          bool PSEAM = false>
+__device__ __forceinline__ bool strip_walk_step(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny,
+                                                int x0, int y0, int y1, bool down, const Coef<C>& k,
+                                                const StripSmem<T, C, NT, NS>& sm, unsigned& G, unsigned& bad,
+                                                long long first_wait = kWaitLimit)
+{
+    StepRow<T, C, COLL, FORC> row{fout, nx, (size_t)nx * ny};
+    return strip_walk<T, C, NT, NS, CARRY, HALO1, PSEAM>(fin, nx, ny, x0, y0, y1, down, k, sm, G, bad, row,
+                                                         first_wait);
+}
+
 // One lattice, grid (strips, row chunks).  MINB > 1 asks the compiler to fit
 // MINB CTAs per SM in the register file (at the price of spills if needed).
 template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY, int MINB, bool HALO1, bool PSEAM>
 __global__ void __launch_bounds__(NT, MINB)
 k_step_strip(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, int nchunks, Coef<C> k,
-             unsigned* __restrict__ status)
+             unsigned* __restrict__ status, long long first_wait)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     if (!staged_alignment_ok(smem, fin, fout)) {
@@ -395,8 +426,8 @@ k_step_strip(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, in
     if (y1 <= y0) return;
     strip_init_barriers(sm);
     unsigned G = 0, bad = 0;
-    strip_walk<T, C, COLL, FORC, NT, NS, CARRY, HALO1, PSEAM>(fin, fout, nx, ny, x0, y0, y1, (blockIdx.y & 1) != 0,
-                                                              k, sm, G, bad);
+    strip_walk_step<T, C, COLL, FORC, NT, NS, CARRY, HALO1, PSEAM>(fin, fout, nx, ny, x0, y0, y1,
+                                                                   (blockIdx.y & 1) != 0, k, sm, G, bad, first_wait);
     flag_status(bad, status);
 }
 
@@ -410,7 +441,8 @@ constexpr size_t strip_smem()
 // chunks as fill every resident CTA slot once (one wave), but no chunk shorter
 // than 16 rows, so the two halo rows per chunk stay a small overhead.
 template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY, int MINB, bool HALO1, bool PSEAM>
-int launch_strip_cfg(const lbm_params* p, const void* fin, void* fout, unsigned* status, cudaStream_t s)
+int launch_strip_cfg(const lbm_params* p, const void* fin, void* fout, unsigned* status, cudaStream_t s,
+                     long long first_wait)
 {
     constexpr size_t smem = strip_smem<T, C, NT, NS>();
     auto kern = k_step_strip<T, C, COLL, FORC, NT, NS, CARRY, MINB, HALO1, PSEAM>;
@@ -429,23 +461,25 @@ int launch_strip_cfg(const lbm_params* p, const void* fin, void* fout, unsigned*
     int nchunks = std::max(1, (nsm * per_sm) / nstrips);
     nchunks = std::min(nchunks, std::max(1, p->ny / 16));
     const Coef<C> k = make_coef<C>(*p);
-    kern<<<dim3(nstrips, nchunks), NT, smem, s>>>((const T*)fin, (T*)fout, p->nx, p->ny, nchunks, k, status);
+    kern<<<dim3(nstrips, nchunks), NT, smem, s>>>((const T*)fin, (T*)fout, p->nx, p->ny, nchunks, k, status,
+                                                  first_wait);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_E_CUDA;
 }
 
 template <typename T, typename C, int NT, int NS, bool CARRY = false, int MINB = 1, bool HALO1 = false,
           bool PSEAM = false>
-int launch_strip_scheme(const lbm_params* p, const void* fin, void* fout, unsigned* status, cudaStream_t s)
+int launch_strip_scheme(const lbm_params* p, const void* fin, void* fout, unsigned* status, cudaStream_t s,
+                        long long first_wait = kWaitLimit)
 {
     if (p->collision == LBM_MRT)
-        return launch_strip_cfg<T, C, MRT, GUO, NT, NS, CARRY, MINB, HALO1, PSEAM>(p, fin, fout, status, s);
+        return launch_strip_cfg<T, C, MRT, GUO, NT, NS, CARRY, MINB, HALO1, PSEAM>(p, fin, fout, status, s, first_wait);
     if (p->forcing == LBM_GUO)
-        return launch_strip_cfg<T, C, BGK, GUO, NT, NS, CARRY, MINB, HALO1, PSEAM>(p, fin, fout, status, s);
+        return launch_strip_cfg<T, C, BGK, GUO, NT, NS, CARRY, MINB, HALO1, PSEAM>(p, fin, fout, status, s, first_wait);
     if (p->forcing == LBM_EDM)
-        return launch_strip_cfg<T, C, BGK, EDM, NT, NS, CARRY, MINB, HALO1, PSEAM>(p, fin, fout, status, s);
+        return launch_strip_cfg<T, C, BGK, EDM, NT, NS, CARRY, MINB, HALO1, PSEAM>(p, fin, fout, status, s, first_wait);
     if (p->forcing == LBM_LI)
-        return launch_strip_cfg<T, C, BGK, LI, NT, NS, CARRY, MINB, HALO1, PSEAM>(p, fin, fout, status, s);
-    return launch_strip_cfg<T, C, BGK, SC, NT, NS, CARRY, MINB, HALO1, PSEAM>(p, fin, fout, status, s);
+        return launch_strip_cfg<T, C, BGK, LI, NT, NS, CARRY, MINB, HALO1, PSEAM>(p, fin, fout, status, s, first_wait);
+    return launch_strip_cfg<T, C, BGK, SC, NT, NS, CARRY, MINB, HALO1, PSEAM>(p, fin, fout, status, s, first_wait);
 }
 
 }  // namespace lbm

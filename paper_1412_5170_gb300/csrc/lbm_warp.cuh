@@ -105,7 +105,8 @@ __device__ __forceinline__ C halo_psi(const float* __restrict__ st, int lane, in
 template <typename C, int COLL, int FORC, int NS, bool CARRY>
 __device__ __forceinline__ bool warp_walk(const float* __restrict__ fin, float* __restrict__ fout, int nx, int ny,
                                           int x0, int y0, int y1, bool down, const Coef<C>& k,
-                                          const WarpSmem<NS>& sm, unsigned& G, unsigned& bad)
+                                          const WarpSmem<NS>& sm, unsigned& G, unsigned& bad,
+                                          long long first_wait = kWaitLimit)
 {
     constexpr int SW = WarpSmem<NS>::SW;
     const int lane = threadIdx.x & 31;
@@ -160,7 +161,8 @@ __device__ __forceinline__ bool warp_walk(const float* __restrict__ fin, float* 
     auto body = [&](int kk, C (&gn)[9][4], C (&gc)[9][4]) -> bool {
         const unsigned g = base + kk;
         const float* st = sm.stages + (g % NS) * 9 * SW;
-        if (!__all_sync(kFull, mbar_wait(&sm.bars[g % NS], (g / NS) & 1))) return false;
+        if (!__all_sync(kFull, mbar_wait(&sm.bars[g % NS], (g / NS) & 1, kk == 0 ? first_wait : kWaitLimit)))
+            return false;
         pull4_warp<C>(st, c0, lane, lane_hl, gn);
         const C hn = halo_psi<C>(st, lane, wp, k, mybad);
         if constexpr (CARRY) {
@@ -267,7 +269,7 @@ __device__ __forceinline__ void warp_init_barriers(const WarpSmem<NS>& sm)
 template <typename C, int COLL, int FORC, int NS, bool CARRY>
 __global__ void __launch_bounds__(32, CARRY ? 12 : 16)
 k_step_warp(const float* __restrict__ fin, float* __restrict__ fout, int nx, int ny, int nchunks, Coef<C> k,
-            unsigned* __restrict__ status)
+            unsigned* __restrict__ status, long long first_wait)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     if (!staged_alignment_ok(smem, fin, fout)) {
@@ -281,12 +283,14 @@ k_step_warp(const float* __restrict__ fin, float* __restrict__ fout, int nx, int
     if (y1 <= y0) return;
     warp_init_barriers(sm);
     unsigned G = 0, bad = 0;
-    warp_walk<C, COLL, FORC, NS, CARRY>(fin, fout, nx, ny, x0, y0, y1, (blockIdx.y & 1) != 0, k, sm, G, bad);
+    warp_walk<C, COLL, FORC, NS, CARRY>(fin, fout, nx, ny, x0, y0, y1, (blockIdx.y & 1) != 0, k, sm, G, bad,
+                                        first_wait);
     flag_status(bad, status);
 }
 
 template <typename C, int COLL, int FORC, int NS, bool CARRY>
-int launch_warp_cfg(const lbm_params* p, const void* fin, void* fout, unsigned* status, cudaStream_t s)
+int launch_warp_cfg(const lbm_params* p, const void* fin, void* fout, unsigned* status, cudaStream_t s,
+                    long long first_wait)
 {
     constexpr size_t smem = warp_smem<NS>();
     auto kern = k_step_warp<C, COLL, FORC, NS, CARRY>;
@@ -304,18 +308,20 @@ int launch_warp_cfg(const lbm_params* p, const void* fin, void* fout, unsigned* 
     int nchunks = std::max(1, (nsm * per_sm) / nstrips);
     nchunks = std::min(nchunks, std::max(1, p->ny / 16));
     const Coef<C> k = make_coef<C>(*p);
-    kern<<<dim3(nstrips, nchunks), 32, smem, s>>>((const float*)fin, (float*)fout, p->nx, p->ny, nchunks, k, status);
+    kern<<<dim3(nstrips, nchunks), 32, smem, s>>>((const float*)fin, (float*)fout, p->nx, p->ny, nchunks, k, status,
+                                                  first_wait);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_E_CUDA;
 }
 
 template <int NS, bool CARRY>
-int launch_warp_scheme(const lbm_params* p, const void* fin, void* fout, unsigned* status, cudaStream_t s)
+int launch_warp_scheme(const lbm_params* p, const void* fin, void* fout, unsigned* status, cudaStream_t s,
+                       long long first_wait = kWaitLimit)
 {
-    if (p->collision == LBM_MRT) return launch_warp_cfg<float, MRT, GUO, NS, CARRY>(p, fin, fout, status, s);
-    if (p->forcing == LBM_GUO) return launch_warp_cfg<float, BGK, GUO, NS, CARRY>(p, fin, fout, status, s);
-    if (p->forcing == LBM_EDM) return launch_warp_cfg<float, BGK, EDM, NS, CARRY>(p, fin, fout, status, s);
-    if (p->forcing == LBM_LI) return launch_warp_cfg<float, BGK, LI, NS, CARRY>(p, fin, fout, status, s);
-    return launch_warp_cfg<float, BGK, SC, NS, CARRY>(p, fin, fout, status, s);
+    if (p->collision == LBM_MRT) return launch_warp_cfg<float, MRT, GUO, NS, CARRY>(p, fin, fout, status, s, first_wait);
+    if (p->forcing == LBM_GUO) return launch_warp_cfg<float, BGK, GUO, NS, CARRY>(p, fin, fout, status, s, first_wait);
+    if (p->forcing == LBM_EDM) return launch_warp_cfg<float, BGK, EDM, NS, CARRY>(p, fin, fout, status, s, first_wait);
+    if (p->forcing == LBM_LI) return launch_warp_cfg<float, BGK, LI, NS, CARRY>(p, fin, fout, status, s, first_wait);
+    return launch_warp_cfg<float, BGK, SC, NS, CARRY>(p, fin, fout, status, s, first_wait);
 }
 
 }  // namespace lbm

@@ -105,6 +105,7 @@ _PROTOS = {
     "lbm_write_populations": (ctypes.c_int, [_vp, _vp]),
     "lbm_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
     "lbm_load": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+    "lbm_inject_stage_timeout": (ctypes.c_int, [_vp]),
     "lbm_get_variant": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "lbm_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "lbm_config_count": (ctypes.c_int, [ctypes.POINTER(lbm_params), ctypes.POINTER(ctypes.c_int)]),
@@ -158,6 +159,12 @@ def check(status, what=""):
     if status != OK:
         raise LbmError(status, what)
     return status
+
+
+def strip_observation(p: lbm_params) -> bool:
+    """Whether lbm_stats observes p's lattice with the strip walk (one launch,
+    reduction included): the lattices the strip kernel takes, nx % 4 == 0."""
+    return p.nx >= 4 and p.nx % 4 == 0
 
 
 def tc() -> float:
@@ -334,6 +341,11 @@ class Lattice:
                   "lbm_config_describe")
             out.append((i, t.value, s_.value, v.value))
         return out
+
+    def inject_stage_timeout(self):
+        """The next step's staged kernels give up their first stage wait at
+        once (the timeout path, for failure-detection tests)."""
+        check(lbm_inject_stage_timeout(self.ctx), "lbm_inject_stage_timeout")
 
     def autotune(self, trial_steps: int = 20):
         """Time every kernel configuration on this lattice and keep the fastest;
