@@ -9,6 +9,7 @@
 #pragma once
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 
 namespace lbm {
 
@@ -95,6 +96,17 @@ __device__ __forceinline__ float sqrt_nr(float s)   // s > 0
     return std::sqrt(s);
 #endif
 }
+// The bits of a float as an unsigned integer.
+__device__ __forceinline__ unsigned float_bits(float x)
+{
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(x);
+#else
+    unsigned u;
+    std::memcpy(&u, &x, sizeof u);
+    return u;
+#endif
+}
 // x c for a constant c = hi + lo held as two floats.
 __device__ __forceinline__ float mul_split(float x, float hi, float lo) { return fma_rn(x, hi, x * lo); }
 constexpr float kTwoThirdsHi = 0x1.555556p-1f, kTwoThirdsLo = -0x1.555556p-26f;   // 2/3
@@ -145,9 +157,11 @@ __device__ __forceinline__ C psi_of_rho(C rho, const Coef<C>& k, unsigned& bad)
         // liquid) in one fused multiply-add
         const float q = div_nr(num, den);
         const float s = fma_rn(-2.f * k.K * rho, fma_rn(k.T, q, -rho), mul_split(rho, kTwoThirdsHi, kTwoThirdsLo));
-        const bool ok = (rho > 0.f) && (rho < 1.f) && (s >= 0.f);
-        if (!ok) bad |= ST_EOS;
-        return (ok && s > 0.f) ? sqrt_nr(s) : 0.f;
+        // 0 < rho < 1 in one unsigned compare of the bits (negative values,
+        // zero and NaN fall outside)
+        const bool in = float_bits(rho) - 1u < float_bits(1.0f) - 1u;
+        if (!(in && s >= 0.f)) bad |= ST_EOS;
+        return (in && s > 0.f) ? sqrt_nr(s) : 0.f;
     } else {
         const C p = k.K * (rho * k.T * cdiv(num, den) - rho * rho);
         const C s = C(2) * (rho * (C(1) / C(3)) - p);
@@ -233,9 +247,9 @@ __device__ __forceinline__ void collide_f32(float g[9], float Fx, float Fy, cons
     moments(g, drho, jx, jy);
     const float rho = k.rho_ref + drho;
     const float inv_rho = rcp_nr(rho);
-    const float ux = jx * inv_rho, uy = jy * inv_rho;
-    vx = ux + 0.5f * Fx * inv_rho;
-    vy = uy + 0.5f * Fy * inv_rho;
+    // v = (j + F/2) / rho (u itself only where the scheme uses it)
+    vx = fma_rn(0.5f, Fx, jx) * inv_rho;
+    vy = fma_rn(0.5f, Fy, jy) * inv_rho;
     rho_out = rho;
     if constexpr (COLL == BGK && (FORC == GUO || FORC == LI)) {
         // Eqs. 1, 2, 23 (Li et al.: Eq. 31, v' in the source's second-order
@@ -262,6 +276,7 @@ __device__ __forceinline__ void collide_f32(float g[9], float Fx, float Fy, cons
         }
     } else if constexpr (COLL == BGK && FORC == EDM) {
         // Eqs. 1, 22: omega f^eq(u) + [f^eq(u + du) - f^eq(u)] = w36 (omega X + D) / 36
+        const float ux = jx * inv_rho, uy = jy * inv_rho;
         const float usq = 1.5f * (ux * ux + uy * uy);
         const float dux = Fx * inv_rho, duy = Fy * inv_rho;
         const float dq = 1.5f * (dux * (2.f * ux + dux) + duy * (2.f * uy + duy));
@@ -276,6 +291,7 @@ __device__ __forceinline__ void collide_f32(float g[9], float Fx, float Fy, cons
         }
     } else if constexpr (COLL == BGK && FORC == SC) {
         // Eqs. 20-21, the shift tau F / rho with tau = 1/omega as hi + lo
+        const float ux = jx * inv_rho, uy = jy * inv_rho;
         const float tx = Fx * inv_rho, ty = Fy * inv_rho;
         const float uex = ux + mul_split(tx, k.tau, k.tau_lo), uey = uy + mul_split(ty, k.tau, k.tau_lo);
         const float usq = 1.5f * (uex * uex + uey * uey);

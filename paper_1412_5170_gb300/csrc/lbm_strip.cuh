@@ -243,10 +243,12 @@ struct StepRow {
 #pragma unroll
             for (int a = 0; a < 9; ++a) gj[a] = gc[a][j];
             collide<C, COLL, FORC>(gj, Fx, Fy, k, vx, vy, rho, q.c);
-            if (!isfinite(gj[0])) bad |= ST_NONFINITE;   // g0 depends on all the others
 #pragma unroll
             for (int a = 0; a < 9; ++a) o[a][j] = T(gj[a]);
         }
+        // g0 depends on all the others, and a sum of four stays non-finite
+        // if one is (the populations are far below overflow)
+        if (!isfinite((o[0][0] + o[0][1]) + (o[0][2] + o[0][3]))) bad |= ST_NONFINITE;
         T* out = fout + (size_t)y * nx + x;
 #pragma unroll
         for (int a = 0; a < 9; ++a) stg4(out + a * n, o[a][0], o[a][1], o[a][2], o[a][3]);
