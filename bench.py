@@ -178,9 +178,18 @@ def initial_density(lbm, synth, seed):
     return synth.density_field(N_SIDE, N_SIDE, "droplet_array", rl, rv, RADIUS, seed=seed, cell=CELL), rv
 
 
-def cpu_oracle_rate(steps: int, side: int, seed: int):
+def host_cores() -> int:
+    """Host cores this process may use (nproc)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_oracle_rate(steps: int, side: int, seed: int, threads: int = 1):
     """MLUPS of the FP64 CPU oracle, as it stands, on a side x side periodic
-    sample of the workload (one 256 x 256 droplet cell when side = 256)."""
+    sample of the workload (one 256 x 256 droplet cell when side = 256), with
+    its lattice loops on `threads` host threads."""
     import oracle
     from oracle import coexistence as cx
     from paper_1412_5170_gb300 import synth
@@ -189,9 +198,13 @@ def cpu_oracle_rate(steps: int, side: int, seed: int):
                                cell=side)
     q = oracle.params(side, side, T_OVER_TC, TAU, A_PAPER, K_EOS, "mrt", "guo", **MRT)
     f = oracle.init_rest(rho0)
-    t0 = time.perf_counter()
-    _, st = oracle.run(q, f, steps)
-    el = time.perf_counter() - t0
+    oracle.set_threads(threads)
+    try:
+        t0 = time.perf_counter()
+        _, st = oracle.run(q, f, steps)
+        el = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(1)
     return side * side * steps / el / 1e6, el
 
 
@@ -200,20 +213,22 @@ def run_reference(args):
     if rank != 0:
         return
     # Bounded per-step sample: one oracle step on a side x side periodic window,
-    # sized so warmup + steps stay within about two minutes on one host core.
+    # on every host core, sized so warmup + steps stay within about two
+    # minutes even at one core's rate.
+    cores = host_cores()
     total = args.steps + args.warmup
     side = 256 if total * 65536 / 1.5e6 < 120 else (128 if total * 16384 / 1.5e6 < 120 else 64)
     if args.warmup:
-        cpu_oracle_rate(args.warmup, side, SEED)
-    rate, el = cpu_oracle_rate(args.steps, side, SEED)
+        cpu_oracle_rate(args.warmup, side, SEED, cores)
+    rate, el = cpu_oracle_rate(args.steps, side, SEED, cores)
     line = {"impl": "reference", "metric": "MLUPS", "value": rate, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": workload_config({"sample": "%dx%d periodic window per step" % (side, side)}),
-            "cpu_baseline": {"value": rate, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": "%d oracle steps on a %dx%d periodic window of the workload"
-                                       % (args.steps, side, side)},
+            "cpu_baseline": {"value": rate, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": "%d oracle steps on a %dx%d periodic window of the workload, lattice "
+                                       "loops over rows on %d host threads" % (args.steps, side, side, cores)},
             "e2e": {"value": rate, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -316,7 +331,11 @@ def run_ours(args):
         achieved = BYTES_PER_NODE * nodes / (kernel_ms * 1e-3) / 1e9
         traffic = TRAFFIC_CAPTURES.get((kernel_hash(), chosen[0], N_SIDE))
         cpu_steps = args.cpu_steps
+        cores = host_cores()
         cpu_rate, cpu_el = cpu_oracle_rate(cpu_steps, CELL, SEED) if cpu_steps > 0 else (None, 0.0)
+        # all host cores: four times the sample (the same few seconds of wall time on ~16 cores)
+        cpu_all, cpu_all_el = (cpu_oracle_rate(4 * cpu_steps, CELL, SEED, cores) if cpu_steps > 0 and cores > 1
+                               else (cpu_rate, cpu_el))
         line = {
             "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / max(args.steps, 1), "higher_is_better": True,
@@ -332,9 +351,13 @@ def run_ours(args):
                          "kernel": kernel_name(chosen), "kernel_ms": kernel_ms,
                          "bytes_per_node": BYTES_PER_NODE, "algorithmic_bytes": BYTES_PER_NODE * nodes,
                          "traffic_unit": "DRAM bytes read + written per launch (ncu)"},
-            "cpu_baseline": {"value": cpu_rate, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": "%d FP64 oracle steps on one 256x256 droplet cell (%.1f s)"
-                                       % (cpu_steps, cpu_el)},
+            "cpu_baseline": {"value": cpu_all, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": "%d FP64 oracle steps on one 256x256 droplet cell, lattice loops over rows "
+                                       "on %d host threads (%.1f s)" % (4 * cpu_steps if cores > 1 else cpu_steps,
+                                                                         cores, cpu_all_el),
+                             "single_core": {"value": cpu_rate, "cores": 1,
+                                             "sample": "%d FP64 oracle steps on one 256x256 droplet cell (%.1f s)"
+                                                       % (cpu_steps, cpu_el)}},
             "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": 8 * nodes,
                     "d2h_bytes_per_step": 24 * nodes,
                     "how": "lbm_init_density_async(pinned host rho0) + lbm_step(%d) + "
@@ -394,9 +417,14 @@ def run_warmstart(args):
     nodes = np.array([d["side"] ** 2 for d in test], dtype=np.float64)
 
     # The plain method: cold FP64 single-lattice runs to the same criterion,
-    # one instance at a time, on a subset of the instances both runs solved.
+    # one instance at a time (each with its autotuned kernel), on a stated
+    # seeded subset: the first ws_fp64 held-out instances (index order) that
+    # both batched runs solve.  The batched FP32 runs are repeated on exactly
+    # that subset, so the wall times compare the same work; the comparison
+    # counts only instances whose FP32 coexistence densities (cold and warm)
+    # are within the FP32 tolerance (1e-4 relative) of the FP64 run's.
     fp64 = []
-    sub = list(np.nonzero(both)[0][:args.ws_fp64])
+    sub = [int(i) for i in np.nonzero(both)[0][:args.ws_fp64]]
     for i in sub:
         d = test[i]
         p = lbm.make_params(d["side"], d["side"], d["T_over_Tc"], d["tau"], A, d["K"], "mrt", "guo", "fp64",
@@ -407,14 +435,37 @@ def run_warmstart(args):
             torch.cuda.synchronize()
             ts = time.perf_counter()
             st_code, steps, probes = fp64_run_to_steady(lat, d["kind"], args.ws_tol, 1000, args.ws_max_steps)
-            fp64.append(dict(i=int(i), status=st_code, steps=steps, wall_s=time.perf_counter() - ts,
-                             nodes=int(nodes[i]), rho_l=probes[0], rho_v=probes[1],
-                             cold_fp32_rel=[abs(rl_c[i] - probes[0]) / probes[0], abs(rv_c[i] - probes[1]) / probes[1]],
-                             warm_fp32_rel=[abs(rl_w[i] - probes[0]) / probes[0], abs(rv_w[i] - probes[1]) / probes[1]]))
+            fp64.append(dict(i=i, status=st_code, steps=steps, wall_s=time.perf_counter() - ts,
+                             nodes=int(nodes[i]), rho_l=probes[0], rho_v=probes[1]))
+    sub_inst64 = [test[i] for i in sub]
+    cold64 = ws.solve(sub_inst64, **crit) if sub else None
+    warm64 = ws.solve(sub_inst64, warm=net, **crit) if sub else None
     fp64_rate = (sum(r["steps"] * r["nodes"] for r in fp64) / max(sum(r["wall_s"] for r in fp64), 1e-9)
                  if fp64 else None)
-    # FP64 wall projected over every instance both runs solved: its measured
-    # node-step rate times the node-steps the cold runs needed.
+    fp64_cmp = None
+    if sub:
+        rl_c64, rv_c64 = ws.coexistence(sub_inst64, cold64["obs"])
+        rl_w64, rv_w64 = ws.coexistence(sub_inst64, warm64["obs"])
+        for j, r in enumerate(fp64):
+            r["fp32_cold"] = dict(steps=int(cold64["steps"][j]), rel=[abs(rl_c64[j] - r["rho_l"]) / r["rho_l"],
+                                                                      abs(rv_c64[j] - r["rho_v"]) / r["rho_v"]])
+            r["fp32_warm"] = dict(steps=int(warm64["steps_total"][j]), rel=[abs(rl_w64[j] - r["rho_l"]) / r["rho_l"],
+                                                                           abs(rv_w64[j] - r["rho_v"]) / r["rho_v"]])
+        ok64 = [r["status"] == 0 and cold64["state"][j] == lbm.CONVERGED and warm64["state"][j] == lbm.CONVERGED
+                and max(r["fp32_cold"]["rel"] + r["fp32_warm"]["rel"]) < 1e-4 for j, r in enumerate(fp64)]
+        fp64_wall = sum(r["wall_s"] for r in fp64)
+        fp64_cmp = {"instances": len(fp64), "subset": "first %d of the held-out instances both batched runs "
+                                                        "solve, in index order (seed 20145000)" % len(fp64),
+                    "within_fp32_tolerance": int(sum(ok64)),
+                    "fp64_plain_wall_s": fp64_wall,
+                    "fp32_batch_cold_wall_s": cold64["wall_s"], "fp32_batch_warm_wall_s": warm64["wall_s"],
+                    "fp64_over_batch_cold": fp64_wall / cold64["wall_s"],
+                    "fp64_over_batch_warm": fp64_wall / warm64["wall_s"],
+                    "max_rel_error_fp32_vs_fp64": float(max(max(r["fp32_cold"]["rel"] + r["fp32_warm"]["rel"])
+                                                            for r in fp64)),
+                    "fp64_node_steps_per_s": fp64_rate}
+    # FP64 wall projected over every instance both runs solved (context only):
+    # its measured node-step rate times the node-steps the cold runs needed.
     fp64_projected = (float(np.sum(cold["steps"][both] * nodes[both])) / fp64_rate) if fp64_rate else None
 
     def stats(x):
@@ -424,8 +475,8 @@ def run_warmstart(args):
     # wall time is otherwise set by the instances neither run converges
     # within max_steps): both runs again on that subset alone.
     sub_inst = [test[i] for i in np.nonzero(both)[0]]
-    cold_sub = ws.solve(sub_inst, **crit)
-    warm_sub = ws.solve(sub_inst, warm=net, **crit)
+    cold_sub = ws.solve(sub_inst, trace=True, **crit)
+    warm_sub = ws.solve(sub_inst, warm=net, trace=True, **crit)
 
     # instances whose warm and cold steady states differ by more than 1 %
     odd = [dict(i=int(i), kind=test[i]["kind"], side=test[i]["side"], size=round(test[i]["size"], 2),
@@ -458,7 +509,10 @@ def run_warmstart(args):
         "different_steady_state": odd,
         "wall_s_converged_set": {"cold": cold_sub["wall_s"], "warm": warm_sub["wall_s"],
                                  "instances": len(sub_inst),
-                                 "cold_converged": int(conv(cold_sub).sum()), "warm_converged": int(conv(warm_sub).sum())},
+                                 "cold_converged": int(conv(cold_sub).sum()), "warm_converged": int(conv(warm_sub).sum()),
+                                 "per_interval": {"columns": ["running instances", "running nodes", "wall_s"],
+                                                  "cold": cold_sub["trace"], "warm": warm_sub["trace"]}},
+        "fp64_plain_vs_batch": fp64_cmp,
         "wall_s": {"cold_batch": cold["wall_s"], "warm_batch": warm["wall_s"], "perfect_profile_batch": ceil["wall_s"],
                    "train_data": gen["wall_s"], "training": train_s, "fp64_plain_projected": fp64_projected,
                    "total": time.perf_counter() - t0},
@@ -643,29 +697,109 @@ def _solution(fn, *a):
         return None, None
 
 
+# FP64 flops per node update of the FP64 MRT+Guo step (2 per DFMA, 1 per DADD
+# or DMUL), counted by ncu on one launch of the autotuned kernel
+# (sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on.sum / nodes),
+# keyed like TRAFFIC_CAPTURES: sha256 of the kernel sources, configuration
+# id, lattice side; unknown otherwise.
+FP64_FLOPS_CAPTURES: dict = {}
+
+
+def run_fp64(args):
+    """The FP64 step against its own roofline.  On this GPU the FP64 pipe is a
+    small fraction of the FP32 one, so the FP64 step (the parity path) is
+    bound by double-precision arithmetic, not by HBM: report the measured FP64
+    and FP32 fused-multiply-add peaks (lbm_fma_peak), the autotuned FP64
+    MRT+Guo step on the droplet-array workload at side --fp64-size, and its
+    FP64 flop rate as a fraction of the FP64 peak (flops per node from an ncu
+    count, FP64_FLOPS_CAPTURES), beside its HBM fraction at 144 B per node."""
+    import torch
+
+    from paper_1412_5170_gb300 import lbm, synth
+
+    torch.cuda.set_device(0)
+    peak64, peak32 = lbm.fma_peak("fp64"), lbm.fma_peak("fp32")
+    side = args.fp64_size
+    rv, rl = lbm.maxwell(T_OVER_TC)
+    cell = max(32, side // 16)
+    rho0 = synth.density_field(side, side, "droplet_array", rl, rv, RADIUS * cell / CELL, seed=SEED, cell=cell)
+    p = lbm.make_params(side, side, T_OVER_TC, TAU, A_PAPER, K_EOS, "mrt", "guo", "fp64", **MRT)
+    with lbm.Lattice(p) as lat:
+        lat.init_density(rho0)
+        cfg, _ = lat.autotune(5)
+        for _ in range(args.warmup):
+            lat.step(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(lat.stream)
+        for _ in range(args.steps):
+            lat.step(1)
+        e1.record(lat.stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        st = lat.stats()
+    nodes = side * side
+    peak_hbm, kind = measured_peaks()
+    fpn = FP64_FLOPS_CAPTURES.get((kernel_hash(), cfg, side))
+    line = {"metric": "FP64 step: node updates per second and FP64 roofline", "unit": "MLUPS",
+            "value": nodes / (ms * 1e-3) / 1e6, "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+            "config": {"workload": "droplet array %dx%d (cells of %d), T/Tc=0.7, tau=0.8, MRT+Guo, FP64"
+                                   % (side, side, cell), "kernel_config": cfg},
+            "fma_peak_tflops": {"fp64": peak64, "fp32": peak32, "how": "lbm_fma_peak: independent FMA chains, "
+                                                                        "CUDA events, best of 5"},
+            "roofline": {"bound": "alu (FP64 pipe)", "flops_per_node": fpn,
+                         "achieved_tflops": fpn * nodes / (ms * 1e-3) / 1e12 if fpn else None,
+                         "peak_tflops": peak64, "frac": (fpn * nodes / (ms * 1e-3) / 1e12 / peak64) if fpn else None},
+            "hbm": {"bytes_per_node": 144, "achieved_gbs": 144.0 * nodes / (ms * 1e-3) / 1e9, "peak_gbs": peak_hbm,
+                    "frac": 144.0 * nodes / (ms * 1e-3) / 1e9 / peak_hbm, "peak_kind": kind},
+            "status": st["status"]}
+    print(json.dumps(line), flush=True)
+
+
 def run_coexistence(args):
     """Coexistence curves of flat interfaces (the data behind Figs. 2-6 and
     Table 6) for the paper's schemes against the Maxwell construction
     (Eq. 19) and the mechanical-stability solution (Eq. 18) of the same eps,
-    both from liblbm's host solvers."""
+    both from liblbm's host solvers.  Each scheme runs as one FP32 batch of
+    8 x 128 slabs over the temperature grid (the batched engine; a batch
+    holds one scheme); every slab also runs alone on the FP64 path, and the
+    table gives both and their difference."""
+    import numpy as np
+
     from paper_1412_5170_gb300 import lbm
 
     t0 = time.perf_counter()
     temps = [0.5, 0.55, 0.6, 0.65, 0.7, 0.75, 0.8, 0.85, 0.9, 0.95]
-    rows = []
+    rows, batch_s, fp64_s = [], 0.0, 0.0
     for label, coll, forc, A, K, sigma, eps in COEX_SCHEMES:
-        for T in temps:
-            st, rl, rg = coexistence_curve(lbm, coll, forc, A, K, sigma, T, args.coex_steps)
+        inst = [dict(nx=8, ny=128, kind="slab", T_over_Tc=T, tau=1.0, A=A, K=K, size=32.0, seed=11) for T in temps]
+        tb = time.perf_counter()
+        with lbm.Batch(inst, collision=coll, forcing=forc, sigma=sigma, **MRT) as b:
+            b.init()
+            b.step(args.coex_steps)
+            b.observe()
+            _, code, _, obs = b.results()
+        batch_s += time.perf_counter() - tb
+        for j, T in enumerate(temps):
+            tf = time.perf_counter()
+            st64, rl64, rg64 = coexistence_curve(lbm, coll, forc, A, K, sigma, T, args.coex_steps)
+            fp64_s += time.perf_counter() - tf
+            rl, rg, st = float(obs["rho_row_mid"][j]), float(obs["rho_row0"][j]), int(code[j])
             mg, ml = _solution(lbm.mechanical, T, K, eps)
             xg, xl = lbm.maxwell(T)
+            ok = st == 0 and np.isfinite(rl) and np.isfinite(rg)
             rows.append(dict(scheme=label, T=T, status=st, rho_l=rl, rho_g=rg, mech=[ml, mg], maxwell=[xl, xg],
-                             rel_mech=[rl / ml - 1, rg / mg - 1] if st == 0 and mg else None,
-                             rel_maxwell=[rl / xl - 1, rg / xg - 1] if st == 0 else None))
-            print("  %-16s T %.2f status %d rho_l %.6f rho_g %.6g  mech %s %s  maxwell %.6f %.6g" % (
-                label, T, st, rl, rg, ml, mg, xl, xg), file=sys.stderr, flush=True)
+                             rel_mech=[rl / ml - 1, rg / mg - 1] if ok and mg else None,
+                             rel_maxwell=[rl / xl - 1, rg / xg - 1] if ok else None,
+                             fp64=dict(status=st64, rho_l=rl64, rho_g=rg64,
+                                       fp32_rel=[rl / rl64 - 1, rg / rg64 - 1] if ok and st64 == 0 else None)))
+            print("  %-16s T %.2f status %d rho_l %.6f rho_g %.6g (FP64 %d %.6g)  mech %s %s  maxwell %.6f %.6g" % (
+                label, T, st, rl, rg, st64, rg64, ml, mg, xl, xg), file=sys.stderr, flush=True)
     line = {"metric": "flat-interface coexistence densities vs Eqs. 18-19", "unit": "relative deviation",
             "rows": rows, "steps": args.coex_steps, "wall_s": time.perf_counter() - t0,
-            "config": {"workload": "slab 8x128 (half-width 32), FP64, tau = 1, MRT rates 0.8/0.8/1.1"}}
+            "batched_fp32_wall_s": batch_s, "fp64_single_lattices_wall_s": fp64_s,
+            "config": {"workload": "slab 8x128 (half-width 32), tau = 1, MRT rates 0.8/0.8/1.1; one FP32 batch "
+                                   "per scheme over the temperatures, each slab also alone in FP64"}}
     print(json.dumps(line), flush=True)
 
 
@@ -745,7 +879,9 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="throughput", choices=["throughput", "warmstart", "sweep", "coexistence", "batch", "laplace"])
+    ap.add_argument("--mode", default="throughput",
+                    choices=["throughput", "warmstart", "sweep", "coexistence", "batch", "laplace", "fp64"])
+    ap.add_argument("--fp64-size", type=int, default=1024, help="lattice side of --mode fp64")
     ap.add_argument("--laplace-steps", type=int, default=30000)
     ap.add_argument("--batch-n", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=200)
@@ -755,7 +891,7 @@ def main():
     ap.add_argument("--ws-train", type=int, default=2000)
     ap.add_argument("--ws-test", type=int, default=256)
     ap.add_argument("--ws-epochs", type=int, default=3000)
-    ap.add_argument("--ws-fp64", type=int, default=4, help="held-out instances also run on the FP64 path")
+    ap.add_argument("--ws-fp64", type=int, default=64, help="held-out instances also run on the FP64 path")
     ap.add_argument("--ws-A", type=float, default=-0.84, help="Eq. 6 weight A of the sweep (epsilon = -2A = 1.68)")
     ap.add_argument("--ws-tol", type=float, default=1e-5, help="coexistence-density change per 1000 steps")
     ap.add_argument("--ws-max-steps", type=int, default=100000)
@@ -785,6 +921,8 @@ def main():
         run_batch(args)
     elif args.mode == "laplace":
         run_laplace(args)
+    elif args.mode == "fp64":
+        run_fp64(args)
     else:
         run_ours(args)
 

@@ -135,6 +135,14 @@ int lbm_maxwell(double T_over_Tc, double *rho_v, double *rho_l);
  * (0, 1), K <= 0, or no root is bracketed. */
 int lbm_mechanical(double T_over_Tc, double K, double eps, double *rho_v, double *rho_l);
 
+/* Fused multiply-add throughput of the current GPU in TFLOP/s (2 flops per
+ * FMA), FP64 (precision = LBM_FP64) or FP32 (LBM_FP32_DEV), from a kernel of
+ * independent FMA chains timed with CUDA events (best of five launches).
+ * The roofline of the FP64 step, which is bound by double-precision
+ * arithmetic on this GPU; measurement only, the paper has no counterpart.
+ * Synchronises the device. */
+int lbm_fma_peak(int precision, double *tflops);
+
 /* ---- single-lattice context ---- */
 
 /* Device bytes a context needs for p (populations x2, moment and snapshot
@@ -273,10 +281,13 @@ int lbm_autotune(lbm_ctx *ctx, int trial_steps, int *config, double *ms_per_step
  * synchronous; the batch owns its device memory and its CUDA stream. */
 typedef struct {
     int32_t collision;   /* lbm_collision */
-    int32_t forcing;     /* lbm_forcing (MRT: Guo only; not LBM_LI) */
+    int32_t forcing;     /* lbm_forcing (MRT: Guo only) */
     int32_t precision;   /* LBM_FP32_DEV */
     int32_t reserved;    /* 0 */
     double s_e, s_eps, s_q;   /* MRT rates shared by all instances */
+    double sigma;        /* LBM_LI: Li et al.'s sigma shared by all instances
+                            (every instance then needs A = 0, Eq. 4's force;
+                            see lbm_params); 0 for the other forcings */
 } lbm_batch_params;
 
 /* One instance: lattice, model parameters (as in lbm_params) and its initial

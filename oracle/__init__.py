@@ -42,8 +42,11 @@ def build(force: bool = False) -> str:
         return os.environ["ORACLE_SO"]
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        try:   # OpenMP over rows for the multi-core CPU baseline; plain if the compiler lacks it
+            subprocess.check_call(cmd[:1] + ["-fopenmp"] + cmd[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(cmd)
         os.replace(tmp, _SO)
     return _SO
 
@@ -81,6 +84,8 @@ def _lib():
         lib.orc_step.argtypes = [pp, dp, dp]
         lib.orc_run.argtypes = [pp, dp, ctypes.c_int64]
         lib.orc_init_rest.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
+        lib.orc_get_threads.restype = ctypes.c_int
         _lib_handle = lib
     return _lib_handle
 
@@ -94,6 +99,16 @@ def params(nx, ny, T_over_Tc, tau, A, K=1.0, collision="bgk", forcing="guo",
            s_e=1.0, s_eps=1.0, s_q=1.0, sigma=0.0) -> Params:
     return Params(int(nx), int(ny), _COLL[collision], _FORC[forcing], float(T_over_Tc),
                   float(tau), float(A), float(K), float(s_e), float(s_eps), float(s_q), float(sigma))
+
+
+def set_threads(n: int) -> None:
+    """Host threads of the lattice loops (1 by default; results are the same
+    bit for bit for any count)."""
+    _lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return _lib().orc_get_threads()
 
 
 # ---- thermodynamics (Sec. 4.1, Eqs. 7, 29, 30) ----

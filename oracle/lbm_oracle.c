@@ -13,7 +13,9 @@
  *
  * Every function follows the paper's equations in the paper's order, one
  * node at a time, with no blocking or fusion.  Compiled with
- * -O2 -ffp-contract=off (no FMA contraction), round to nearest.
+ * -O2 -ffp-contract=off (no FMA contraction), round to nearest.  The
+ * lattice loops may run on several host threads (OpenMP over rows, see
+ * orc_set_threads); nodes are independent, so results do not depend on it.
  *
  * Population layout: f[(a*ny + y)*nx + x], a = 0..8, double.
  * Velocity numbering (Sec. 2, text after Eq. 2):
@@ -74,6 +76,13 @@ static const double W[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
                             1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
 
 static int wrap(int i, int n) { int r = i % n; return r < 0 ? r + n : r; }
+
+/* Host threads of the lattice loops (OpenMP over rows when compiled with
+ * it).  Every node is computed independently and written to its own place,
+ * so the result is the same bit for bit for any thread count.  Default 1. */
+static int orc_threads = 1;
+void orc_set_threads(int n) { orc_threads = n > 0 ? n : 1; }
+int orc_get_threads(void) { return orc_threads; }
 
 /* ---------------- Sec. 4.1: Carnahan-Starling EOS ---------------- */
 
@@ -142,6 +151,7 @@ void orc_force(int nx, int ny, const double *psi, double A, double *Fx, double *
     const double G = -1.0;
     const double wforce[9] = {0.0, 1.0 / 3, 1.0 / 3, 1.0 / 3, 1.0 / 3,
                               1.0 / 12, 1.0 / 12, 1.0 / 12, 1.0 / 12};
+#pragma omp parallel for num_threads(orc_threads) schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             double sumU[2] = {0.0, 0.0}, sumP[2] = {0.0, 0.0};
@@ -221,6 +231,19 @@ static void matvec9(const double M[81], const double x[9], double y[9])
  * (u = sum f e / rho); Fx, Fy: Eq. 6 force; psi: Eq. 7 effective density at
  * the node (used by Li et al.'s model only).  Writes the post-collision
  * populations to fstar. */
+/* M and its inverse depend on nothing but the lattice: built once (before
+ * any threaded loop, see orc_step). */
+static double M[81], Minv[81];
+static int tables_ready = 0;
+static void mrt_tables(void)
+{
+    if (!tables_ready) {
+        orc_mrt_matrix(M);
+        orc_invert9(M, Minv);
+        tables_ready = 1;
+    }
+}
+
 void orc_collide_node(const orc_params *p, const double f[9], double rho, double ux, double uy,
                       double Fx, double Fy, double psi, double fstar[9])
 {
@@ -258,15 +281,9 @@ void orc_collide_node(const orc_params *p, const double f[9], double rho, double
         /* Eq. 34 with Guo's source in moment space: m = M f, m^eq = M f^eq(rho, v),
          * S = M F_a / (1 - 1/(2 tau)), m* = m - Lambda (m - m^eq) + (I - Lambda/2) S,
          * f* = M^-1 m*. */
-        static double M[81], Minv[81];
-        static int tables_ready = 0;
         double m[9], meq[9], Sm[9], mstar[9];
         double vx = ux + Fx / (2.0 * rho), vy = uy + Fy / (2.0 * rho);
-        if (!tables_ready) {  /* M and its inverse depend on nothing but the lattice */
-            orc_mrt_matrix(M);
-            orc_invert9(M, Minv);
-            tables_ready = 1;
-        }
+        mrt_tables();
         orc_feq(rho, vx, vy, feq);
         orc_guo_source(1.0, Fx, Fy, vx, vy, S);  /* F_a / (1 - 1/(2 tau)) */
         matvec9(M, f, m);
@@ -291,6 +308,8 @@ int orc_macro(const orc_params *p, const double *f, double *rho_o, double *ux_o,
     double *rho = malloc(sizeof(double) * n), *ux = malloc(sizeof(double) * n),
            *uy = malloc(sizeof(double) * n), *psi = malloc(sizeof(double) * n),
            *Fx = malloc(sizeof(double) * n), *Fy = malloc(sizeof(double) * n);
+    int bad = 0;
+#pragma omp parallel for num_threads(orc_threads) schedule(static) reduction(|: bad)
     for (int i = 0; i < n; ++i) {
         double r = 0.0, jx = 0.0, jy = 0.0;
         for (int a = 0; a < 9; ++a) {
@@ -303,10 +322,12 @@ int orc_macro(const orc_params *p, const double *f, double *rho_o, double *ux_o,
         ux[i] = jx / r;
         uy[i] = jy / r;
         double s = orc_psi2(r, T, p->K);
-        if (!(r > 0.0 && r < 1.0) || !(s >= 0.0)) { status = ORC_E_EOS_DOMAIN; s = 0.0; }
+        if (!(r > 0.0 && r < 1.0) || !(s >= 0.0)) { bad = 1; s = 0.0; }
         psi[i] = sqrt(s);
     }
+    if (bad) status = ORC_E_EOS_DOMAIN;
     orc_force(nx, ny, psi, p->A, Fx, Fy);
+#pragma omp parallel for num_threads(orc_threads) schedule(static)
     for (int i = 0; i < n; ++i) {
         if (rho_o) rho_o[i] = rho[i];
         if (ux_o) ux_o[i] = ux[i];
@@ -330,7 +351,9 @@ int orc_step(const orc_params *p, const double *f, double *fnext)
     double *rho = malloc(sizeof(double) * n), *ux = malloc(sizeof(double) * n),
            *uy = malloc(sizeof(double) * n), *Fx = malloc(sizeof(double) * n),
            *Fy = malloc(sizeof(double) * n), *psi = malloc(sizeof(double) * n);
-    int status = orc_macro(p, f, rho, ux, uy, psi, Fx, Fy, NULL, NULL);
+    int status = orc_macro(p, f, rho, ux, uy, psi, Fx, Fy, NULL, NULL), nonfinite = 0;
+    if (p->collision == ORC_MRT) mrt_tables();
+#pragma omp parallel for num_threads(orc_threads) schedule(static) reduction(|: nonfinite)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             int i = y * nx + x;
@@ -339,10 +362,11 @@ int orc_step(const orc_params *p, const double *f, double *fnext)
             orc_collide_node(p, fl, rho[i], ux[i], uy[i], Fx[i], Fy[i], psi[i], fs);
             for (int a = 0; a < 9; ++a) {
                 int xd = wrap(x + EX[a], nx), yd = wrap(y + EY[a], ny);
-                if (!isfinite(fs[a])) status = status ? status : ORC_E_NONFINITE;
+                if (!isfinite(fs[a])) nonfinite = 1;
                 fnext[a * n + yd * nx + xd] = fs[a];
             }
         }
+    if (nonfinite && !status) status = ORC_E_NONFINITE;
     free(rho); free(ux); free(uy); free(Fx); free(Fy); free(psi);
     return status;
 }

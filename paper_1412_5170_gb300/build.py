@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "liblbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["lbm_api.cu", "lbm_observe.cu", "lbm_strip.cu", "lbm_strip_f32.cu", "lbm_pipe_f32.cu", "lbm_strip_f64.cu", "lbm_noalloc.cu", "lbm_batch.cu", "lbm_batch_strip.cu", "lbm_mlp.cu", "lbm_host.cpp"]
+SOURCES = ["lbm_api.cu", "lbm_observe.cu", "lbm_strip.cu", "lbm_strip_f32.cu", "lbm_pipe_f32.cu", "lbm_strip_f64.cu", "lbm_noalloc.cu", "lbm_batch.cu", "lbm_batch_strip.cu", "lbm_mlp.cu", "lbm_peak.cu", "lbm_host.cpp"]
 
 
 def nvcc() -> str:

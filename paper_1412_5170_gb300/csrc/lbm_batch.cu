@@ -492,6 +492,7 @@ struct lbm_batch {
     BItem* items = nullptr;
     int nitems = 0;
     int items_cap = 0;
+    int items_for = 0;           // running instances when the work items were last built
     int* state = nullptr;        // device
     int* fail = nullptr;         // device
     unsigned* status = nullptr;  // device, per instance
@@ -556,11 +557,16 @@ int build_items(lbm_batch* b, const int* host_state)
         const BInst& I = b->hinst[i];
         strip_rows += (long long)((I.nx + b->cols - 1) / b->cols) * I.ny;
     }
+    // About 16 items per SM: while many instances run, items of the tuned
+    // height; as they converge, shorter ones (down to 4 rows), so that the
+    // last few instances still spread over the whole GPU.
     const long long target = 16LL * nsm;
-    const int rows = (int)std::max<long long>(std::min<long long>(b->rows, strip_rows / target), std::min(16, b->rows));
+    const int rows = (int)std::max<long long>(std::min<long long>(b->rows, strip_rows / target), std::min(4, b->rows));
     std::vector<BItem> it;
+    b->items_for = 0;
     for (int i = 0; i < b->n; ++i) {
         if (host_state && host_state[i] != B_RUNNING) continue;
+        b->items_for += 1;
         const BInst& I = b->hinst[i];
         const int nstrips = (I.nx + b->cols - 1) / b->cols;
         const int nch = std::max(1, (I.ny + rows / 2) / rows);
@@ -615,6 +621,7 @@ int launch_batch_scheme(lbm_batch* b, const float* fin, float* fout)
     if (b->collision == LBM_MRT) return launch_batch_step<MRT, GUO, NS, CARRY>(b, fin, fout);
     if (b->forcing == LBM_GUO) return launch_batch_step<BGK, GUO, NS, CARRY>(b, fin, fout);
     if (b->forcing == LBM_EDM) return launch_batch_step<BGK, EDM, NS, CARRY>(b, fin, fout);
+    if (b->forcing == LBM_LI) return launch_batch_step<BGK, LI, NS, CARRY>(b, fin, fout);
     return launch_batch_step<BGK, SC, NS, CARRY>(b, fin, fout);
 }
 
@@ -700,7 +707,6 @@ int lbm_batch_create(const lbm_batch_params* bp, const lbm_instance* inst, int n
     if (!bp || !inst || n < 1 || !out) return LBM_E_INVALID;
     *out = nullptr;
     if (bp->precision != LBM_FP32_DEV) return LBM_E_UNSUPPORTED;
-    if (bp->forcing == LBM_LI) return LBM_E_UNSUPPORTED;   // the batch carries no sigma
     lbm_batch* b = new (std::nothrow) lbm_batch();
     if (!b) return LBM_E_INVALID;
     b->n = n;
@@ -728,6 +734,7 @@ int lbm_batch_create(const lbm_batch_params* bp, const lbm_instance* inst, int n
         p.s_e = bp->s_e;
         p.s_eps = bp->s_eps;
         p.s_q = bp->s_q;
+        p.sigma = bp->sigma;
         double rv = in.rho_v, rl = in.rho_l;
         if (rv <= 0 || rl <= 0) {
             if (lbm_maxwell(in.T_over_Tc, &rv, &rl) != LBM_OK) { delete b; return LBM_E_INVALID; }
@@ -940,7 +947,6 @@ int lbm_batch_run_to_steady(lbm_batch* b, double tol_v, double tol_rho, double t
     int64_t done = 0;
     int active = 0;
     for (int i = 0; i < b->n; ++i) active += b->h_state[i] == B_RUNNING;
-    int items_for = active;
     std::vector<int> before(b->n);
     while (done < max_steps && active > 0) {
         const int64_t k = std::min<int64_t>(check_every, max_steps - done);
@@ -961,10 +967,9 @@ int lbm_batch_run_to_steady(lbm_batch* b, double tol_v, double tol_rho, double t
         b->total_steps += k;
         active = 0;
         for (int i = 0; i < b->n; ++i) active += b->h_state[i] == B_RUNNING;
-        if (active > 0 && active * 4 < items_for * 3) {   // compact the work items to the running instances
+        if (active > 0 && active * 4 < b->items_for * 3) {   // compact the work items to the running instances
             s = build_items(b, b->h_state);
             if (s != LBM_OK) return s;
-            items_for = active;
         }
     }
     if (steps_done) *steps_done = done;

@@ -100,6 +100,7 @@ int launch_scheme(int collision, int forcing, const BatchLaunch& L)
     if (forcing == LBM_GUO) return launch_cfg<BGK, GUO, NT, NS, CARRY, MINB, PSEAM>(L);
     if (forcing == LBM_EDM) return launch_cfg<BGK, EDM, NT, NS, CARRY, MINB, PSEAM>(L);
     if (forcing == LBM_SC) return launch_cfg<BGK, SC, NT, NS, CARRY, MINB, PSEAM>(L);
+    if (forcing == LBM_LI) return launch_cfg<BGK, LI, NT, NS, CARRY, MINB, PSEAM>(L);
     return LBM_E_INVALID;
 }
 

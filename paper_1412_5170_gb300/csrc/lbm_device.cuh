@@ -247,9 +247,12 @@ __device__ __forceinline__ void collide_f32(float g[9], float Fx, float Fy, cons
     moments(g, drho, jx, jy);
     const float rho = k.rho_ref + drho;
     const float inv_rho = rcp_nr(rho);
-    // v = (j + F/2) / rho (u itself only where the scheme uses it)
-    vx = fma_rn(0.5f, Fx, jx) * inv_rho;
-    vy = fma_rn(0.5f, Fy, jy) * inv_rho;
+    const float ux = jx * inv_rho, uy = jy * inv_rho;
+    // v = u + F/(2 rho).  (Written as (j + F/2)/rho, algebraically the same,
+    // a narrow FP32 slab's total momentum wandered 50 times further from
+    // zero -- 6e-5 against 1e-6 over 1e5 steps -- and the slab drifted.)
+    vx = ux + 0.5f * Fx * inv_rho;
+    vy = uy + 0.5f * Fy * inv_rho;
     rho_out = rho;
     if constexpr (COLL == BGK && (FORC == GUO || FORC == LI)) {
         // Eqs. 1, 2, 23 (Li et al.: Eq. 31, v' in the source's second-order
@@ -276,7 +279,6 @@ __device__ __forceinline__ void collide_f32(float g[9], float Fx, float Fy, cons
         }
     } else if constexpr (COLL == BGK && FORC == EDM) {
         // Eqs. 1, 22: omega f^eq(u) + [f^eq(u + du) - f^eq(u)] = w36 (omega X + D) / 36
-        const float ux = jx * inv_rho, uy = jy * inv_rho;
         const float usq = 1.5f * (ux * ux + uy * uy);
         const float dux = Fx * inv_rho, duy = Fy * inv_rho;
         const float dq = 1.5f * (dux * (2.f * ux + dux) + duy * (2.f * uy + duy));
@@ -291,7 +293,6 @@ __device__ __forceinline__ void collide_f32(float g[9], float Fx, float Fy, cons
         }
     } else if constexpr (COLL == BGK && FORC == SC) {
         // Eqs. 20-21, the shift tau F / rho with tau = 1/omega as hi + lo
-        const float ux = jx * inv_rho, uy = jy * inv_rho;
         const float tx = Fx * inv_rho, ty = Fy * inv_rho;
         const float uex = ux + mul_split(tx, k.tau, k.tau_lo), uey = uy + mul_split(ty, k.tau, k.tau_lo);
         const float usq = 1.5f * (uex * uex + uey * uey);

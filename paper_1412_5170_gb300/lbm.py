@@ -53,7 +53,7 @@ class lbm_stats_t(ctypes.Structure):
 class lbm_batch_params(ctypes.Structure):
     _fields_ = [("collision", ctypes.c_int32), ("forcing", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double),
-                ("s_q", ctypes.c_double)]
+                ("s_q", ctypes.c_double), ("sigma", ctypes.c_double)]
 
 
 class lbm_profile_geom(ctypes.Structure):
@@ -86,6 +86,7 @@ _PROTOS = {
     "lbm_version": (ctypes.c_int, []),
     "lbm_tc": (ctypes.c_double, []),
     "lbm_mechanical": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _dp]),
+    "lbm_fma_peak": (ctypes.c_int, [ctypes.c_int, _dp]),
     "lbm_maxwell": (ctypes.c_int, [ctypes.c_double, _dp, _dp]),
     "lbm_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(lbm_params), ctypes.POINTER(ctypes.c_size_t)]),
     "lbm_create": (ctypes.c_int, [ctypes.POINTER(lbm_params), _vp, _vp, ctypes.c_size_t, ctypes.POINTER(_vp)]),
@@ -165,6 +166,13 @@ def strip_observation(p: lbm_params) -> bool:
     """Whether lbm_stats observes p's lattice with the strip walk (one launch,
     reduction included): the lattices the strip kernel takes, nx % 4 == 0."""
     return p.nx >= 4 and p.nx % 4 == 0
+
+
+def fma_peak(precision: str = "fp64") -> float:
+    """Measured FMA throughput of the current GPU (TFLOP/s) in FP64 or FP32."""
+    t = ctypes.c_double()
+    check(lbm_fma_peak(PRECISION[precision], ctypes.byref(t)), "lbm_fma_peak")
+    return t.value
 
 
 def tc() -> float:
@@ -372,9 +380,9 @@ class Batch:
     A, K, size and optional width (4), rho_l / rho_v (0: Maxwell), cell, seed,
     noise_amp (1e-6)."""
 
-    def __init__(self, instances, collision="bgk", forcing="guo", s_e=0.8, s_eps=0.8, s_q=1.1):
+    def __init__(self, instances, collision="bgk", forcing="guo", s_e=0.8, s_eps=0.8, s_q=1.1, sigma=0.0):
         bp = lbm_batch_params(COLLISION[collision], FORCING[forcing], FP32_DEV, 0, float(s_e), float(s_eps),
-                              float(s_q))
+                              float(s_q), float(sigma))
         arr = (lbm_instance * len(instances))()
         for i, d in enumerate(instances):
             nx = int(d.get("nx", d.get("side")))

@@ -146,7 +146,7 @@ def _rest_init(b, instances, prof, size, use, mass0, keep=None, newton=2):
 
 
 def solve(instances, collision="mrt", tol_v=0.0, tol_rho=0.0, tol_coex=1e-5, check_every=1000, max_steps=100000,
-          warm=None, profiles=None, sizes=None, fallback="failed", tune=True):
+          warm=None, profiles=None, sizes=None, fallback="failed", tune=True, trace=False):
     """Run a batch to steady state.
 
     warm: a trained WarmStart (predicts every instance it has a network for);
@@ -174,7 +174,9 @@ def solve(instances, collision="mrt", tol_v=0.0, tol_rho=0.0, tol_coex=1e-5, che
     grids centred on them), which instances were warm-started and which fell
     back, the warm run's own outcome before any fallback (`first`), and the
     wall time of everything (initialisation, prediction, mass matching and
-    fallback runs included)."""
+    fallback runs included).  trace: also step the batch one check interval
+    per call and return, per interval, the instances and nodes still running
+    and its wall time (`trace`; the first run only)."""
     import torch
     n = len(instances)
     with lbm.Batch(instances, collision=collision) as b:
@@ -207,8 +209,22 @@ def solve(instances, collision="mrt", tol_v=0.0, tol_rho=0.0, tol_coex=1e-5, che
                 centre_used = _rest_init(b, instances, prof, size, use & ~uniform, mass0, keep=uniform)
         if tune:
             b.autotune(3)
-        st, done = b.run_to_steady(tol_v=tol_v, tol_rho=tol_rho, tol_coex=tol_coex, check_every=check_every,
-                                   max_steps=max_steps)
+        intervals = []
+        if trace:
+            sides = np.array([shape(d)[0] * shape(d)[1] for d in instances], dtype=np.float64)
+            done = 0
+            st = lbm.E_NOT_CONVERGED
+            while done < max_steps and st == lbm.E_NOT_CONVERGED:
+                running = b.results()[0] == lbm.RUNNING
+                torch.cuda.synchronize()
+                ti = time.perf_counter()
+                st, d = b.run_to_steady(tol_v=tol_v, tol_rho=tol_rho, tol_coex=tol_coex, check_every=check_every,
+                                        max_steps=min(check_every, max_steps - done))
+                intervals.append((int(running.sum()), float(sides[running].sum()), time.perf_counter() - ti))
+                done += d
+        else:
+            st, done = b.run_to_steady(tol_v=tol_v, tol_rho=tol_rho, tol_coex=tol_coex, check_every=check_every,
+                                       max_steps=max_steps)
         state, code, steps, obs = b.results()
         eq_size, geom = converged_geometry(instances, state, obs)
         prof_out = b.profiles(NB, geom)
@@ -245,7 +261,7 @@ def solve(instances, collision="mrt", tol_v=0.0, tol_rho=0.0, tol_coex=1e-5, che
             prof_out[i] = r2["profiles"][j]
     return dict(status=st, steps_done=done, state=state, code=code, steps=steps, steps_total=steps_total, obs=obs,
                 sizes=eq_size, profiles=prof_out, warm=use, fallback=redo, first=first,
-                wall_s=wall, nodes=nodes)
+                wall_s=wall, nodes=nodes, trace=intervals)
 
 
 class WarmStart:

@@ -254,8 +254,31 @@ def test_batch_tuning_rejects_unknown_shapes(lbm):
         b.set_tuning(512, 3, 32, True)
 
 
-def test_batch_rejects_li_forcing(lbm):
-    """The batch carries no sigma: Li et al.'s model runs on single lattices."""
-    inst = instances()[:1]
+@pytest.mark.parametrize("tuning", [(128, 3, 16, False), (512, 2, 16, True)])
+def test_batch_li_model_matches_oracle(lbm, tuning):
+    """Li et al.'s model (Sec. 4.3, Eq. 31; Eq. 4's force, A = 0) in a batch,
+    with sigma shared by the batch, against the oracle: per-node density
+    within the FP32 element-wise bar after 80 steps, on the one-warp walk and
+    the 512-column block walk."""
+    inst = [dict(d, A=0.0) for d in wide_instances()[:2]]
+    steps, sigma = 80, 0.105
+    with lbm.Batch(inst, collision="bgk", forcing="li", sigma=sigma) as b:
+        b.set_tuning(*tuning)
+        b.init()
+        b.step(steps)
+        got = [b.read_density(i) for i in range(len(inst))]
+    for i, d in enumerate(inst):
+        nx, ny = d.get("nx", d.get("side")), d.get("ny", d.get("side"))
+        rv, rl = lbm.maxwell(d["T_over_Tc"])
+        rho0 = synth.density_field(nx, ny, d["kind"], rl, rv, d["size"], seed=d["seed"])
+        q = oracle.params(nx, ny, d["T_over_Tc"], d["tau"], 0.0, d["K"], "bgk", "li", sigma=sigma)
+        f, _ = oracle.run(q, oracle.init_rest(rho0), steps)
+        ref = f.sum(0)
+        assert (np.abs(got[i] - ref) / ref).max() < 2e-5
+
+
+def test_batch_li_model_needs_eq4_force(lbm):
+    """Li et al.'s model takes Eq. 4's force (A = 0 in Eq. 6); a batch whose
+    instance has another A is rejected, as a single lattice would be."""
     with pytest.raises(lbm.LbmError):
-        lbm.Batch(inst, collision="bgk", forcing="li")
+        lbm.Batch(instances()[:1], collision="bgk", forcing="li", sigma=0.105)

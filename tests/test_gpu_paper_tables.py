@@ -13,6 +13,14 @@ rho_l at the corner node, Us_max = max |v| (readings 10-11).
   0), which the library reports; the densities still match.
 * Table 5 (Li et al.'s model, sigma = 0.105): rho_g within 2 % at tau = 0.8
   and 1, 10 % at tau = 1.5; its rise with tau is reproduced.
+* Table 7 (Sec. 4.4.2, MRT, "the same parameters as Table 4"): with Table 4's
+  eps = 1.68 the MRT bubble keeps the BGK gas density (0.0043 against the
+  printed 0.0021 -- at leading order the relaxation rates do not move the
+  coexistence densities); the printed values follow eps = 1.4 (A = -0.7):
+  rho_g within 7 % (0.1 %, 3.7 %, 6.5 % at tau_nu = 0.7, 1, 1.5 with the
+  rates 0.8 / 0.8 / 1.1, which the paper does not state), rho_l within
+  0.2 %, and rho_g falls with tau_nu as printed.  Us_max is not compared: it
+  follows the unstated rates.
 """
 import json
 import os
@@ -23,8 +31,9 @@ pytestmark = pytest.mark.gpu
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
 
 
-def bubble(lbm, forcing, tau, A, K, sigma=0.0, steps=30000):
-    p = lbm.make_params(100, 100, 0.6, tau, A, K, "bgk", forcing, "fp64", sigma=sigma)
+def bubble(lbm, forcing, tau, A, K, sigma=0.0, steps=30000, collision="bgk"):
+    p = lbm.make_params(100, 100, 0.6, tau, A, K, collision, forcing, "fp64", sigma=sigma,
+                        s_e=0.8, s_eps=0.8, s_q=1.1)
     with lbm.Lattice(p) as lat:
         lat.init_preset("bubble", 23.0, seed=1)
         lat.autotune(3)   # the fastest kernel for this small lattice (the state does not advance)
@@ -63,3 +72,18 @@ def test_table5_li_tau_sweep(lbm):
         assert st["max_v"] == pytest.approx(row["us_max"], rel=0.15)
         rg.append(st["rho_center"])
     assert rg[0] < rg[1] < rg[2]   # gas density rises with tau (Sec. 4.3.2)
+
+
+def test_table7_mrt_bubble_follows_eps_1_4(lbm):
+    rows = GOLD["table7"]["rows"]
+    rg = []
+    for row in rows:
+        st = bubble(lbm, "guo", row["tau_nu"], -0.7, 1.0, collision="mrt")
+        assert st["status"] == 0
+        assert st["rho_center"] == pytest.approx(row["rho_g"], rel=0.07)
+        assert st["rho_corner"] == pytest.approx(row["rho_l"], rel=2e-3)
+        rg.append(st["rho_center"])
+    assert rg[0] > rg[1] > rg[2]
+    # Table 4's eps = 1.68 gives the BGK gas density again, twice the printed one
+    st = bubble(lbm, "guo", 1.0, -0.84, 1.0, collision="mrt")
+    assert st["rho_center"] > 1.8 * rows[1]["rho_g"]

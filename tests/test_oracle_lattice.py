@@ -212,3 +212,29 @@ def test_droplets_follow_laplace_law(orc):
     assert slope > 0
     assert np.max(np.abs(fit - ys)) < 0.01 * max(ys)      # a straight line in 1/R
     assert abs(icpt) < 0.06 * max(ys)                     # through the origin
+
+
+@pytest.mark.parametrize("coll,forc,tr,steps", [("mrt", "guo", 0.8, 60), ("bgk", "edm", 0.8, 60),
+                                                 ("bgk", "guo", 0.45, 400)])
+def test_threaded_oracle_is_the_single_threaded_one(orc, coll, forc, tr, steps):
+    """The oracle's lattice loops run over rows on several host threads for
+    the multi-core CPU baseline.  Nodes are independent, so the populations
+    must be the same bit for bit as with one thread, and so must the status
+    -- also of a run that leaves the EOS domain (the last case: a sharp
+    droplet at T/Tc = 0.45 with A = -0.84)."""
+    nx, ny = 48, 40
+    rv, rl = 0.0002, 0.46
+    rho0 = synth.density_field(nx, ny, "droplet", rl, rv, 11.0, seed=5, width=2.0)
+    q = orc.params(nx, ny, tr, 0.6, -0.84 if tr < 0.5 else -0.304, 1.0, coll, forc, s_e=0.8, s_eps=0.8, s_q=1.1)
+    f0 = orc.init_rest(rho0)
+    try:
+        orc.set_threads(1)
+        f1, s1 = orc.run(q, f0, steps)
+        orc.set_threads(4)
+        f4, s4 = orc.run(q, f0, steps)
+    finally:
+        orc.set_threads(1)
+    assert s1 == s4
+    assert np.array_equal(f1, f4, equal_nan=True)
+    if tr < 0.5:
+        assert s1 != orc.OK
