@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -39,22 +40,12 @@ BYTES_PER_NODE = 72          # 9 FP32 deviations read + 9 written
 SEED = 20141217 + 2 * 1000
 
 # DRAM bytes (read + write) per launch of the step kernel measured by ncu on
-# the workload above (mean of three launches), keyed by the sha256 of the
-# kernel sources it was taken from, the kernel configuration id and the
-# lattice side; when any of them changes the entry no longer matches and
-# traffic is null.
-# (The captures were taken on these very kernels before their tuning
-# variants -- left halo psi thread, seam copies per lane -- were put side by
-# side in the configuration table, before the FP32 initial-state kernels
-# were added beside them, and before the FP64 collision stopped closing its
-# rest population on the mass -- an `if constexpr` on the compute type that
-# leaves the float code as it was; each FP32 step-kernel variant compiles as
-# it did then.)
+# the workload above (mean of three launches: dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by the sha256 of the kernel sources it was
+# taken from, the kernel configuration id and the lattice side; when any of
+# them changes the entry no longer matches and traffic is null.
 TRAFFIC_CAPTURES: dict = {
-    ("9fc4715a09458c18", 8, 4096): (619.57e6 + 551.43e6),
-    ("9fc4715a09458c18", 9, 4096): (608.67e6 + 548.07e6),
-    ("9fc4715a09458c18", 10, 4096): (604.54e6 + 546.89e6),
-    ("9fc4715a09458c18", 12, 4096): (610.65e6 + 549.48e6),
+    ("705b5ab437de3bc3", 10, 4096): (604.17e6 + 547.01e6),
 }
 # Sources of the block-strip step kernel (its configuration table included).
 KERNEL_SOURCES = ["paper_1412_5170_gb300/csrc/lbm_strip.cuh", "paper_1412_5170_gb300/csrc/lbm_strip_f32.cu",
@@ -388,7 +379,7 @@ def run_warmstart(args):
 
     torch.cuda.set_device(0)
     A = args.ws_A
-    crit = dict(tol_coex=args.ws_tol, check_every=1000, max_steps=args.ws_max_steps)
+    crit = dict(tol_coex=args.ws_tol, check_every=1000, max_steps=args.ws_max_steps, coex_rule=args.ws_rule)
 
     def draw(n, seed):
         inst = synth.batch_instances(n, seed=seed)
@@ -434,7 +425,8 @@ def run_warmstart(args):
             lat.autotune(3)   # the fastest FP64 kernel for this lattice (the state does not advance)
             torch.cuda.synchronize()
             ts = time.perf_counter()
-            st_code, steps, probes = fp64_run_to_steady(lat, d["kind"], args.ws_tol, 1000, args.ws_max_steps)
+            st_code, steps, probes = fp64_run_to_steady(lat, d["kind"], args.ws_tol, 1000, args.ws_max_steps,
+                                                        args.ws_rule)
             fp64.append(dict(i=i, status=st_code, steps=steps, wall_s=time.perf_counter() - ts,
                              nodes=int(nodes[i]), rho_l=probes[0], rho_v=probes[1]))
     sub_inst64 = [test[i] for i in sub]
@@ -526,7 +518,8 @@ def run_warmstart(args):
         "fp64_plain": {"instances": fp64, "node_steps_per_s": fp64_rate},
         "batched_fp32_node_steps_per_s": {"cold": float(np.sum(cold["steps"] * nodes)) / cold["wall_s"],
                                           "warm": float(np.sum(warm["steps"] * nodes)) / warm["wall_s"]},
-        "criterion": {"coexistence_rel_change_per_1000_steps": args.ws_tol, "max_steps": args.ws_max_steps},
+        "criterion": {"coexistence_rel_change_per_1000_steps": args.ws_tol, "max_steps": args.ws_max_steps,
+                      "rule": args.ws_rule},
         "train_loss": losses,
         "config": {"workload": "batched sweep: side in {64..512}, T/Tc U[.5,.9], tau U[.55,1.2], K U[1/16,1], "
                                "R U[10, side/4], droplet or slab; MRT+Guo, A=%g, FP32 deviations" % A},
@@ -573,6 +566,7 @@ def run_batch(args):
         b.init()
         torch.cuda.synchronize()
         t1 = time.perf_counter()
+        b.set_coex_rule(args.ws_rule)
         st, done = b.run_to_steady(tol_coex=args.ws_tol, check_every=1000, max_steps=args.ws_max_steps)
         wall = time.perf_counter() - t1
         state, code, steps, obs = b.results()
@@ -697,12 +691,15 @@ def _solution(fn, *a):
         return None, None
 
 
-# FP64 flops per node update of the FP64 MRT+Guo step (2 per DFMA, 1 per DADD
-# or DMUL), counted by ncu on one launch of the autotuned kernel
+# FP64 instructions per node update of the FP64 MRT+Guo step, counted by ncu
+# on one launch of the autotuned kernel
 # (sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on.sum / nodes),
-# keyed like TRAFFIC_CAPTURES: sha256 of the kernel sources, configuration
-# id, lattice side; unknown otherwise.
-FP64_FLOPS_CAPTURES: dict = {}
+# keyed like TRAFFIC_CAPTURES (sha256 of the kernel sources, configuration
+# id, lattice side); unknown otherwise.
+FP64_INST_CAPTURES: dict = {
+    ("705b5ab437de3bc3", 0, 1024): {"dfma": 73662464 / 1048576, "dadd": 87670784 / 1048576,
+                                    "dmul": 40845312 / 1048576},
+}
 
 
 def run_fp64(args):
@@ -711,8 +708,10 @@ def run_fp64(args):
     bound by double-precision arithmetic, not by HBM: report the measured FP64
     and FP32 fused-multiply-add peaks (lbm_fma_peak), the autotuned FP64
     MRT+Guo step on the droplet-array workload at side --fp64-size, and its
-    FP64 flop rate as a fraction of the FP64 peak (flops per node from an ncu
-    count, FP64_FLOPS_CAPTURES), beside its HBM fraction at 144 B per node."""
+    FP64 instruction issue rate as a fraction of the FP64 pipe's (DFMA, DADD
+    and DMUL per node from an ncu count, FP64_INST_CAPTURES; the pipe issues
+    each of them at the rate of the FMA peak / 2 flops), beside its flop rate
+    and its HBM fraction at 144 B per node."""
     import torch
 
     from paper_1412_5170_gb300 import lbm, synth
@@ -740,18 +739,27 @@ def run_fp64(args):
         st = lat.stats()
     nodes = side * side
     peak_hbm, kind = measured_peaks()
-    fpn = FP64_FLOPS_CAPTURES.get((kernel_hash(), cfg, side))
+    cnt = FP64_INST_CAPTURES.get((kernel_hash(), cfg, side))
+    rate = nodes / (ms * 1e-3)
+    if cnt:
+        ipn = cnt["dfma"] + cnt["dadd"] + cnt["dmul"]
+        fpn = 2 * cnt["dfma"] + cnt["dadd"] + cnt["dmul"]
+        roof = {"bound": "alu", "unit": "FP64 instructions/s", "inst_per_node": ipn, "flops_per_node": fpn,
+                "achieved": ipn * rate, "peak": peak64 * 1e12 / 2, "frac": ipn * rate / (peak64 * 1e12 / 2),
+                "achieved_tflops": fpn * rate / 1e12, "peak_tflops": peak64,
+                "flop_frac": fpn * rate / 1e12 / peak64, "counts": cnt}
+    else:
+        roof = {"bound": "alu", "unit": "FP64 instructions/s", "inst_per_node": None, "frac": None,
+                "peak_tflops": peak64, "note": "no instruction count for this kernel, configuration and size"}
     line = {"metric": "FP64 step: node updates per second and FP64 roofline", "unit": "MLUPS",
-            "value": nodes / (ms * 1e-3) / 1e6, "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+            "value": rate / 1e6, "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
             "config": {"workload": "droplet array %dx%d (cells of %d), T/Tc=0.7, tau=0.8, MRT+Guo, FP64"
                                    % (side, side, cell), "kernel_config": cfg},
             "fma_peak_tflops": {"fp64": peak64, "fp32": peak32, "how": "lbm_fma_peak: independent FMA chains, "
                                                                         "CUDA events, best of 5"},
-            "roofline": {"bound": "alu (FP64 pipe)", "flops_per_node": fpn,
-                         "achieved_tflops": fpn * nodes / (ms * 1e-3) / 1e12 if fpn else None,
-                         "peak_tflops": peak64, "frac": (fpn * nodes / (ms * 1e-3) / 1e12 / peak64) if fpn else None},
-            "hbm": {"bytes_per_node": 144, "achieved_gbs": 144.0 * nodes / (ms * 1e-3) / 1e9, "peak_gbs": peak_hbm,
-                    "frac": 144.0 * nodes / (ms * 1e-3) / 1e9 / peak_hbm, "peak_kind": kind},
+            "roofline": roof,
+            "hbm": {"bytes_per_node": 144, "achieved_gbs": 144.0 * rate / 1e9, "peak_gbs": peak_hbm,
+                    "frac": 144.0 * rate / 1e9 / peak_hbm, "peak_kind": kind},
             "status": st["status"]}
     print(json.dumps(line), flush=True)
 
@@ -852,13 +860,42 @@ def run_laplace(args):
     print(json.dumps(line), flush=True)
 
 
-def fp64_run_to_steady(lat, kind, tol, every, max_steps):
-    """Cold single-lattice run until both coexistence densities (centre and
-    corner, or mid and edge row for a slab) change by less than tol relative
-    per `every` steps -- the batched runs' criterion -- on the FP64 path."""
+def coex_tail(d, dp):
+    """The change still to come of a probe whose last two changes were d and
+    dp, as the batched solver estimates it (LBM_COEX_TAIL): a geometric series
+    of ratio r = d / dp -- |d| r / (1 - r) for 0 <= r < 1, |d| for r < 0,
+    infinite for r >= 1, for an unknown dp (NaN) or dp = 0; zero if d is
+    zero."""
+    if d == 0.0:
+        return 0.0
+    if not dp != 0.0:          # unknown (NaN), or a move after a standstill
+        return math.inf
+    r = d / dp
+    if not r < 1.0:
+        return math.inf
+    return abs(d) if r < 0.0 else abs(d) * r / (1.0 - r)
+
+
+def coex_measure(prev, cur, dprev, rule):
+    """The quantity the coexistence criterion holds below tol_coex: the
+    probes' relative change since the previous check, with rule "tail" also
+    their estimated change still to come (both probes, the larger)."""
+    d = (cur[0] - prev[0], cur[1] - prev[1])
+    m = max(abs(d[0]) / abs(cur[0]), abs(d[1]) / abs(cur[1]))
+    if rule == "tail" and m == m:
+        m = max(m, coex_tail(d[0], dprev[0]) / abs(cur[0]), coex_tail(d[1], dprev[1]) / abs(cur[1]))
+    return m, d
+
+
+def fp64_run_to_steady(lat, kind, tol, every, max_steps, rule="change"):
+    """Cold single-lattice run on the FP64 path until both coexistence
+    densities (centre and corner, or mid and edge row for a slab) meet the
+    batched runs' criterion: relative change below tol per `every` steps and,
+    with rule "tail", so is their estimated change still to come."""
     def probes(st):
         return (st["rho_row_mid"], st["rho_row0"]) if kind == "slab" else (st["rho_center"], st["rho_corner"])
     prev = probes(lat.stats())
+    dprev = (math.nan, math.nan)
     steps = 0
     while steps < max_steps:
         lat.step(every)
@@ -867,7 +904,8 @@ def fp64_run_to_steady(lat, kind, tol, every, max_steps):
         if st["status"] != 0:
             return st["status"], steps, prev
         cur = probes(st)
-        if max(abs(cur[0] - prev[0]) / cur[0], abs(cur[1] - prev[1]) / cur[1]) < tol:
+        m, dprev = coex_measure(prev, cur, dprev, rule)
+        if m < tol:
             return 0, steps, cur
         prev = cur
     return 6, steps, prev
@@ -895,6 +933,8 @@ def main():
     ap.add_argument("--ws-A", type=float, default=-0.84, help="Eq. 6 weight A of the sweep (epsilon = -2A = 1.68)")
     ap.add_argument("--ws-tol", type=float, default=1e-5, help="coexistence-density change per 1000 steps")
     ap.add_argument("--ws-max-steps", type=int, default=100000)
+    ap.add_argument("--ws-rule", default="tail", choices=["change", "tail"],
+                    help="coexistence criterion: change per check, or also the estimated change still to come")
     ap.add_argument("--cpu-steps", type=int, default=700,
                     help="oracle steps on one 256x256 cell for cpu_baseline (0 = skip)")
     ap.add_argument("--size", type=int, default=4096, help="lattice side (multiple of 256; profiling)")

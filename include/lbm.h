@@ -357,6 +357,23 @@ int lbm_batch_step(lbm_batch *b, int64_t nsteps);
 int lbm_batch_run_to_steady(lbm_batch *b, double tol_v, double tol_rho, double tol_coex, int64_t check_every,
                             int64_t max_steps, int64_t *steps_done);
 
+/* How lbm_batch_run_to_steady judges the coexistence probes against
+ * tol_coex (a stopping rule of the measurement; the paper fixes none):
+ *   LBM_COEX_CHANGE  the relative change of each probe since the previous
+ *                    check (the default);
+ *   LBM_COEX_TAIL    also the estimated change still to come: the probe's
+ *                    last two changes d and d' taken as a geometric series of
+ *                    ratio r = d/d' (Aitken's extrapolation) give |d| r/(1-r)
+ *                    for 0 <= r < 1 and |d| for r < 0; while the changes do
+ *                    not shrink (r >= 1), or before three checks, the
+ *                    instance does not stop.  A run that creeps towards its
+ *                    steady state by small, slowly shrinking changes then
+ *                    runs on until what is left is below the tolerance.
+ * Applies from the next check on; LBM_E_INVALID for another value. */
+#define LBM_COEX_CHANGE 0
+#define LBM_COEX_TAIL 1
+int lbm_batch_set_coex_rule(lbm_batch *b, int rule);
+
 /* Recompute the observables of every instance (no decisions, no snapshot change). */
 int lbm_batch_observe(lbm_batch *b);
 

@@ -207,17 +207,36 @@ k_observe_batch(const float* __restrict__ f, const BInst* __restrict__ inst, con
     }
 }
 
+// What is left of a probe's approach to its limit, estimated from its last
+// two changes d (this interval) and dp (the one before) as a geometric series
+// with ratio r = d / dp (Aitken's extrapolation): |d| r / (1 - r) for
+// 0 <= r < 1, |d| for an alternating approach (r < 0, the limit lies within
+// the last change), infinite while the changes do not shrink (r >= 1),
+// before two changes are known (dp NaN) or after a standstill (dp = 0);
+// zero for a probe that did not move.
+__device__ __forceinline__ double coex_tail(double d, double dp)
+{
+    if (d == 0.0) return 0.0;
+    if (!(dp != 0.0)) return HUGE_VAL;
+    const double r = d / dp;
+    if (!(r < 1.0)) return HUGE_VAL;
+    return r < 0.0 ? fabs(d) : fabs(d) * r / (1.0 - r);
+}
+
 // Per-instance fixed-order reduction of the tile partials, then the
 // convergence / failure decision: a running instance stops as converged when
 // max|v - v_snap| < tol_v, max|rho - rho_snap|/rho < tol_rho, or both of its
 // coexistence densities (liquid and vapour probe: centre and corner node of a
 // droplet or bubble, mid and edge row of a slab) changed by less than tol_coex
-// relative since the previous check (a tolerance <= 0 disables it), and as
-// failed when a kernel flagged it.
+// relative since the previous check -- with coex_rule LBM_COEX_TAIL, also
+// their estimated remaining changes (coex_tail) -- (a tolerance <= 0
+// disables it), and as failed when a kernel flagged it.  probe_prev holds
+// each instance's probes at the previous check and their changes then.
 __global__ void __launch_bounds__(256)
 k_reduce_batch(const BInst* __restrict__ inst, const BPart* __restrict__ parts, int* __restrict__ state,
                int* __restrict__ fail_code, const unsigned* __restrict__ inst_status, BObs* __restrict__ obs,
-               double2* __restrict__ probe_prev, double tol_v, double tol_rho, double tol_coex, int decide, int all)
+               double4* __restrict__ probe_prev, double tol_v, double tol_rho, double tol_coex, int coex_rule,
+               int decide, int all)
 {
     const int i = blockIdx.x;
     if (!all && state[i] != B_RUNNING) return;
@@ -259,9 +278,12 @@ k_reduce_batch(const BInst* __restrict__ inst, const BPart* __restrict__ parts, 
         if (!decide || state[i] != B_RUNNING) return;
         const bool slab = I->kind == LBM_SLAB;
         const double pl = slab ? o.rho_row_mid : o.rho_center, pv = slab ? o.rho_row0 : o.rho_corner;
-        const double2 pp = probe_prev[i];
-        const double dcoex = fmax(fabs(pl - pp.x) / fabs(pl), fabs(pv - pp.y) / fabs(pv));   // NaN before the first check
-        probe_prev[i] = make_double2(pl, pv);
+        const double4 pp = probe_prev[i];
+        const double dl = pl - pp.x, dv = pv - pp.y;
+        double dcoex = fmax(fabs(dl) / fabs(pl), fabs(dv) / fabs(pv));   // NaN before the first check
+        if (coex_rule == LBM_COEX_TAIL && dcoex == dcoex)
+            dcoex = fmax(dcoex, fmax(coex_tail(dl, pp.z) / fabs(pl), coex_tail(dv, pp.w) / fabs(pv)));
+        probe_prev[i] = make_double4(pl, pv, dl, dv);
         if (b) {
             state[i] = B_FAILED;
             fail_code[i] = (b & ST_NONFINITE) ? LBM_E_NONFINITE
@@ -498,7 +520,8 @@ struct lbm_batch {
     unsigned* status = nullptr;  // device, per instance
     int* queue = nullptr;        // device: the step's work-item counter and walkers-done counter
     BObs* obs = nullptr;         // device
-    double2* probe_prev = nullptr;   // device: coexistence probes at the previous check
+    double4* probe_prev = nullptr;   // device: coexistence probes at the previous check, and their changes then
+    int coex_rule = LBM_COEX_CHANGE;
     // pinned host mirrors
     int* h_state = nullptr;
     int* h_fail = nullptr;
@@ -658,7 +681,7 @@ int observe(lbm_batch* b, int mode, double tol_v, double tol_rho, double tol_coe
         B_CUDA(cudaGetLastError());
     }
     k_reduce_batch<<<b->n, 256, 0, b->stream>>>(b->dinst, b->parts, b->state, b->fail, b->status, b->obs,
-                                                 b->probe_prev, tol_v, tol_rho, tol_coex, decide,
+                                                 b->probe_prev, tol_v, tol_rho, tol_coex, b->coex_rule, decide,
                                                  (mode & BO_ALL) ? 1 : 0);
     B_CUDA(cudaGetLastError());
     B_CUDA(cudaMemcpyAsync(b->h_state, b->state, sizeof(int) * b->n, cudaMemcpyDeviceToHost, b->stream));
@@ -790,7 +813,7 @@ int lbm_batch_create(const lbm_batch_params* bp, const lbm_instance* inst, int n
     if ((e = cudaMalloc(&b->queue, sizeof(int) * 2)) != cudaSuccess) return fail(e);
     if ((e = cudaMemset(b->queue, 0, sizeof(int) * 2)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&b->obs, sizeof(BObs) * n)) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&b->probe_prev, sizeof(double2) * n)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&b->probe_prev, sizeof(double4) * n)) != cudaSuccess) return fail(e);
     if ((e = cudaMallocHost(&b->h_state, sizeof(int) * n)) != cudaSuccess) return fail(e);
     if ((e = cudaMallocHost(&b->h_fail, sizeof(int) * n)) != cudaSuccess) return fail(e);
     if ((e = cudaMallocHost(&b->h_obs, sizeof(BObs) * n)) != cudaSuccess) return fail(e);
@@ -846,7 +869,7 @@ static int reset_run_state(lbm_batch* b)
     B_CUDA(cudaMemsetAsync(b->fail, 0, sizeof(int) * b->n, b->stream));
     B_CUDA(cudaMemsetAsync(b->status, 0, sizeof(unsigned) * b->n, b->stream));
     B_CUDA(cudaMemsetAsync(b->obs, 0, sizeof(BObs) * b->n, b->stream));
-    B_CUDA(cudaMemsetAsync(b->probe_prev, 0xff, sizeof(double2) * b->n, b->stream));   // NaN: no previous check
+    B_CUDA(cudaMemsetAsync(b->probe_prev, 0xff, sizeof(double4) * b->n, b->stream));   // NaN: no previous check
     long long nodes = 0;
     for (const BInst& I : b->hinst) nodes = std::max<long long>(nodes, I.node_off + (long long)I.nx * I.ny);
     B_CUDA(cudaMemsetAsync(b->snap, 0xff, sizeof(Snap) * nodes, b->stream));   // NaN: no snapshot yet
@@ -974,6 +997,16 @@ int lbm_batch_run_to_steady(lbm_batch* b, double tol_v, double tol_rho, double t
     }
     if (steps_done) *steps_done = done;
     return active == 0 ? LBM_OK : LBM_E_NOT_CONVERGED;
+}
+
+int lbm_batch_set_coex_rule(lbm_batch* b, int rule)
+{
+    if (!b || (rule != LBM_COEX_CHANGE && rule != LBM_COEX_TAIL)) return LBM_E_INVALID;
+    if (rule != b->coex_rule) {
+        b->coex_rule = rule;
+        drop_graphs(b);   // the captured intervals carry the rule as a kernel argument
+    }
+    return LBM_OK;
 }
 
 int lbm_batch_results(lbm_batch* b, int32_t* state, int32_t* code, int64_t* steps, double* obs)

@@ -79,6 +79,7 @@ BATCH_OBS = ("mass", "max_v", "max_dv", "max_drho", "rho_min", "rho_max", "rho_c
              "rho_row_mid", "rho_row0")
 RUNNING, CONVERGED, FAILED = 0, 1, 2
 LBM_INIT_REST = 1
+COEX_RULES = {"change": 0, "tail": 1}   # LBM_COEX_CHANGE, LBM_COEX_TAIL
 
 _vp, _dp, _i64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64
 _PROTOS = {
@@ -128,6 +129,7 @@ _PROTOS = {
     "lbm_batch_read_density": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "lbm_batch_profiles": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "lbm_batch_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "lbm_batch_set_coex_rule": (ctypes.c_int, [_vp, ctypes.c_int]),
     "lbm_batch_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _dp]),
     "lbm_batch_nodes": (ctypes.c_int64, [_vp]),
@@ -442,6 +444,11 @@ class Batch:
 
     def step(self, n: int):
         check(lbm_batch_step(self.h, int(n)), "lbm_batch_step")
+
+    def set_coex_rule(self, rule: str):
+        """How tol_coex is judged: "change" (the probes' change per check) or
+        "tail" (also their estimated change still to come)."""
+        check(lbm_batch_set_coex_rule(self.h, COEX_RULES[rule]), "lbm_batch_set_coex_rule")
 
     def run_to_steady(self, tol_v=0.0, tol_rho=0.0, tol_coex=0.0, check_every=1000, max_steps=10 ** 6):
         done = _i64()

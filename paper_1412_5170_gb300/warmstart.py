@@ -146,7 +146,7 @@ def _rest_init(b, instances, prof, size, use, mass0, keep=None, newton=2):
 
 
 def solve(instances, collision="mrt", tol_v=0.0, tol_rho=0.0, tol_coex=1e-5, check_every=1000, max_steps=100000,
-          warm=None, profiles=None, sizes=None, fallback="failed", tune=True, trace=False):
+          warm=None, profiles=None, sizes=None, fallback="failed", tune=True, trace=False, coex_rule="change"):
     """Run a batch to steady state.
 
     warm: a trained WarmStart (predicts every instance it has a network for);
@@ -176,7 +176,9 @@ def solve(instances, collision="mrt", tol_v=0.0, tol_rho=0.0, tol_coex=1e-5, che
     wall time of everything (initialisation, prediction, mass matching and
     fallback runs included).  trace: also step the batch one check interval
     per call and return, per interval, the instances and nodes still running
-    and its wall time (`trace`; the first run only)."""
+    and its wall time (`trace`; the first run only).  coex_rule: how tol_coex
+    is judged ("change" per check, or "tail": also the estimated change still
+    to come; Batch.set_coex_rule)."""
     import torch
     n = len(instances)
     with lbm.Batch(instances, collision=collision) as b:
@@ -209,6 +211,7 @@ def solve(instances, collision="mrt", tol_v=0.0, tol_rho=0.0, tol_coex=1e-5, che
                 centre_used = _rest_init(b, instances, prof, size, use & ~uniform, mass0, keep=uniform)
         if tune:
             b.autotune(3)
+        b.set_coex_rule(coex_rule)
         intervals = []
         if trace:
             sides = np.array([shape(d)[0] * shape(d)[1] for d in instances], dtype=np.float64)
@@ -248,7 +251,7 @@ def solve(instances, collision="mrt", tol_v=0.0, tol_rho=0.0, tol_coex=1e-5, che
     if redo.any():
         idx = np.nonzero(redo)[0]
         r2 = solve([instances[i] for i in idx], collision, tol_v, tol_rho, tol_coex, check_every, max_steps,
-                   tune=tune)
+                   tune=tune, coex_rule=coex_rule)
         wall += r2["wall_s"]
         state, code, steps = state.copy(), code.copy(), steps.copy()
         obs = {k: v.copy() for k, v in obs.items()}

@@ -113,6 +113,69 @@ def test_coexistence_criterion_stops_when_probes_settle(lbm):
     assert obs["rho_row0"][1] == pytest.approx(ref["rho_row0"][1], rel=1e-3)
 
 
+def _bench():
+    import importlib
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    return importlib.import_module("bench")
+
+
+def test_tail_rule_decides_as_the_host_rule(lbm):
+    """LBM_COEX_TAIL on the device against the host statement of the same
+    rule (bench.coex_measure): stepping one check interval at a time, every
+    instance stops exactly at the first check where its probes' relative
+    change and estimated remaining change are both below tol_coex, and no
+    earlier than under the change-only rule; its probes then sit at least as
+    close to a much longer run's."""
+    bench = _bench()
+    inst = [dict(side=64, kind="droplet", T_over_Tc=0.85, tau=1.0, A=-0.5, K=1.0, size=16.0, seed=11),
+            dict(nx=16, ny=96, kind="slab", T_over_Tc=0.8, tau=0.8, A=-0.5, K=0.5, size=24.0, seed=12),
+            dict(side=96, kind="droplet", T_over_Tc=0.6, tau=0.7, A=-0.84, K=0.25, size=14.0, seed=13)]
+    tol, every = 1e-5, 1000
+    keys = [("rho_row_mid", "rho_row0") if d["kind"] == "slab" else ("rho_center", "rho_corner") for d in inst]
+    with lbm.Batch(inst, collision="mrt") as b:
+        b.init()
+        b.set_coex_rule("tail")
+        prev = [None] * len(inst)
+        dprev = [(float("nan"), float("nan"))] * len(inst)
+        expect = [None] * len(inst)
+        for k in range(1, 200):
+            st, _ = b.run_to_steady(tol_coex=tol, check_every=every, max_steps=every)
+            state, _, steps, obs = b.results()
+            for i in range(len(inst)):
+                if expect[i] is not None:
+                    continue
+                cur = (obs[keys[i][0]][i], obs[keys[i][1]][i])
+                if prev[i] is not None:
+                    m, dprev[i] = bench.coex_measure(prev[i], cur, dprev[i], "tail")
+                    if m < tol:
+                        expect[i] = k * every
+                prev[i] = cur
+                assert (state[i] == lbm.CONVERGED) == (expect[i] is not None), (i, k)
+            if st == lbm.OK:
+                break
+        assert all(e is not None for e in expect)
+        assert list(steps) == expect
+        tail_obs = {key: obs[key].copy() for key in ("rho_center", "rho_corner", "rho_row_mid", "rho_row0")}
+    with lbm.Batch(inst, collision="mrt") as c:
+        c.init()
+        st, _ = c.run_to_steady(tol_coex=tol, check_every=every, max_steps=10 ** 6)
+        assert st == lbm.OK
+        _, _, steps_change, obs_change = c.results()
+    assert all(t >= s for t, s in zip(expect, steps_change))
+    with lbm.Batch(inst, collision="mrt") as r:
+        r.init()
+        r.step(max(expect) + 30000)
+        r.observe()
+        _, _, _, ref = r.results()
+    for i, ks in enumerate(keys):
+        for key in ks:
+            e_tail = abs(tail_obs[key][i] / ref[key][i] - 1)
+            e_change = abs(obs_change[key][i] / ref[key][i] - 1)
+            assert e_tail <= e_change + 1e-6, (i, key, e_tail, e_change)
+
+
 @pytest.mark.parametrize("tuning", TUNINGS)
 def test_graph_intervals_equal_plain_steps(lbm, tuning):
     inst = instances()
