@@ -374,7 +374,10 @@ int lbm_batch_run_to_steady(lbm_batch *b, double tol_v, double tol_rho, double t
 #define LBM_COEX_TAIL 1
 int lbm_batch_set_coex_rule(lbm_batch *b, int rule);
 
-/* Recompute the observables of every instance (no decisions, no snapshot change). */
+/* Recompute the observables of every instance (no convergence decisions, no
+ * snapshot change).  A running instance that a kernel flagged (non-finite or
+ * out-of-domain value) is marked LBM_FAILED with its code, as a check of
+ * lbm_batch_run_to_steady would. */
 int lbm_batch_observe(lbm_batch *b);
 
 /* Host arrays of n entries (any may be NULL): state (LBM_RUNNING /

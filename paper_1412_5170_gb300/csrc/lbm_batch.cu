@@ -230,12 +230,15 @@ __device__ __forceinline__ double coex_tail(double d, double dp)
 // droplet or bubble, mid and edge row of a slab) changed by less than tol_coex
 // relative since the previous check -- with coex_rule LBM_COEX_TAIL, also
 // their estimated remaining changes (coex_tail) -- (a tolerance <= 0
-// disables it), and as failed when a kernel flagged it.  probe_prev holds
+// disables it), and -- with or without a decision -- as failed when a kernel
+// flagged it.  probe_prev holds
 // each instance's probes at the previous check and their changes then.
+struct ProbeHist { double pl, pv, dl, dv; };   // probes at the previous check and their changes then
+
 __global__ void __launch_bounds__(256)
 k_reduce_batch(const BInst* __restrict__ inst, const BPart* __restrict__ parts, int* __restrict__ state,
                int* __restrict__ fail_code, const unsigned* __restrict__ inst_status, BObs* __restrict__ obs,
-               double4* __restrict__ probe_prev, double tol_v, double tol_rho, double tol_coex, int coex_rule,
+               ProbeHist* __restrict__ probe_prev, double tol_v, double tol_rho, double tol_coex, int coex_rule,
                int decide, int all)
 {
     const int i = blockIdx.x;
@@ -275,24 +278,26 @@ k_reduce_batch(const BInst* __restrict__ inst, const BPart* __restrict__ parts, 
         o.rho_max = red[6][0];
         o.rho_min = -red[7][0];
         const unsigned b = sbad[0] | inst_status[i];
-        if (!decide || state[i] != B_RUNNING) return;
-        const bool slab = I->kind == LBM_SLAB;
-        const double pl = slab ? o.rho_row_mid : o.rho_center, pv = slab ? o.rho_row0 : o.rho_corner;
-        const double4 pp = probe_prev[i];
-        const double dl = pl - pp.x, dv = pv - pp.y;
-        double dcoex = fmax(fabs(dl) / fabs(pl), fabs(dv) / fabs(pv));   // NaN before the first check
-        if (coex_rule == LBM_COEX_TAIL && dcoex == dcoex)
-            dcoex = fmax(dcoex, fmax(coex_tail(dl, pp.z) / fabs(pl), coex_tail(dv, pp.w) / fabs(pv)));
-        probe_prev[i] = make_double4(pl, pv, dl, dv);
-        if (b) {
+        if (state[i] != B_RUNNING) return;
+        if (b) {   // a kernel flagged this instance: failed, with or without a decision
             state[i] = B_FAILED;
             fail_code[i] = (b & ST_NONFINITE) ? LBM_E_NONFINITE
                            : (b & ST_EOS) ? LBM_E_EOS_DOMAIN
                            : (b & ST_TIMEOUT) ? LBM_E_TIMEOUT : LBM_E_CUDA;
-        } else if ((tol_v > 0 && o.max_dv < tol_v) || (tol_rho > 0 && o.max_drho < tol_rho) ||
-                   (tol_coex > 0 && dcoex < tol_coex)) {
-            state[i] = B_CONVERGED;
+            return;
         }
+        if (!decide) return;
+        const bool slab = I->kind == LBM_SLAB;
+        const double pl = slab ? o.rho_row_mid : o.rho_center, pv = slab ? o.rho_row0 : o.rho_corner;
+        const ProbeHist pp = probe_prev[i];
+        const double dl = pl - pp.pl, dv = pv - pp.pv;
+        double dcoex = fmax(fabs(dl) / fabs(pl), fabs(dv) / fabs(pv));   // NaN before the first check
+        if (coex_rule == LBM_COEX_TAIL && dcoex == dcoex)
+            dcoex = fmax(dcoex, fmax(coex_tail(dl, pp.dl) / fabs(pl), coex_tail(dv, pp.dv) / fabs(pv)));
+        probe_prev[i] = ProbeHist{pl, pv, dl, dv};
+        if ((tol_v > 0 && o.max_dv < tol_v) || (tol_rho > 0 && o.max_drho < tol_rho) ||
+            (tol_coex > 0 && dcoex < tol_coex))
+            state[i] = B_CONVERGED;
     }
 }
 
@@ -520,7 +525,7 @@ struct lbm_batch {
     unsigned* status = nullptr;  // device, per instance
     int* queue = nullptr;        // device: the step's work-item counter and walkers-done counter
     BObs* obs = nullptr;         // device
-    double4* probe_prev = nullptr;   // device: coexistence probes at the previous check, and their changes then
+    ProbeHist* probe_prev = nullptr;   // device: coexistence probes at the previous check, and their changes then
     int coex_rule = LBM_COEX_CHANGE;
     // pinned host mirrors
     int* h_state = nullptr;
@@ -813,7 +818,7 @@ int lbm_batch_create(const lbm_batch_params* bp, const lbm_instance* inst, int n
     if ((e = cudaMalloc(&b->queue, sizeof(int) * 2)) != cudaSuccess) return fail(e);
     if ((e = cudaMemset(b->queue, 0, sizeof(int) * 2)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&b->obs, sizeof(BObs) * n)) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&b->probe_prev, sizeof(double4) * n)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&b->probe_prev, sizeof(ProbeHist) * n)) != cudaSuccess) return fail(e);
     if ((e = cudaMallocHost(&b->h_state, sizeof(int) * n)) != cudaSuccess) return fail(e);
     if ((e = cudaMallocHost(&b->h_fail, sizeof(int) * n)) != cudaSuccess) return fail(e);
     if ((e = cudaMallocHost(&b->h_obs, sizeof(BObs) * n)) != cudaSuccess) return fail(e);
@@ -869,7 +874,7 @@ static int reset_run_state(lbm_batch* b)
     B_CUDA(cudaMemsetAsync(b->fail, 0, sizeof(int) * b->n, b->stream));
     B_CUDA(cudaMemsetAsync(b->status, 0, sizeof(unsigned) * b->n, b->stream));
     B_CUDA(cudaMemsetAsync(b->obs, 0, sizeof(BObs) * b->n, b->stream));
-    B_CUDA(cudaMemsetAsync(b->probe_prev, 0xff, sizeof(double4) * b->n, b->stream));   // NaN: no previous check
+    B_CUDA(cudaMemsetAsync(b->probe_prev, 0xff, sizeof(ProbeHist) * b->n, b->stream));   // NaN: no previous check
     long long nodes = 0;
     for (const BInst& I : b->hinst) nodes = std::max<long long>(nodes, I.node_off + (long long)I.nx * I.ny);
     B_CUDA(cudaMemsetAsync(b->snap, 0xff, sizeof(Snap) * nodes, b->stream));   // NaN: no snapshot yet

@@ -139,6 +139,7 @@ struct Coef {
     // FP32 path only (see "FP32 arithmetic without biased constants"):
     C A;          // Eq. 6 weight
     C tau_lo;     // tau + tau_lo = 1/omega (Shan-Chen shift: omega tau F = F exactly)
+    C h_e, h_eps, h_q;   // 1 - s/2 of the MRT rates s_e, s_eps, s_q (Eq. 34's source factor), in float
 };
 
 // psi from the K-scaled Carnahan-Starling EOS (Eqs. 29-30, a = 1, b = 4,
@@ -324,15 +325,15 @@ __device__ __forceinline__ void collide_f32(float g[9], float Fx, float Fy, cons
         const float vF6 = 6.f * (vx * Fx + vy * Fy);
         const float se = k.s_e, sp = k.s_eps, sq = k.s_q, sn = k.omega;
         const float b0 = mul_split(drho, kNinthHi, kNinthLo);
-        const float b1 = mul_split((m1 - se * (m1 - (rv2 - 2.f * drho))) + (1.f - 0.5f * se) * vF6,
-                                   k36thHi, k36thLo);
-        const float b2 = mul_split((m2 - sp * (m2 - (drho - rv2))) - (1.f - 0.5f * sp) * vF6,
-                                   k36thHi, k36thLo);
+        // the factors 1 - s/2 come precomputed (k.h_*, and 1 - omega/2 = k.guo_pre), the
+        // same floats the expressions would give, so that no node spends an instruction on them
+        const float b1 = mul_split((m1 - se * (m1 - (rv2 - 2.f * drho))) + k.h_e * vF6, k36thHi, k36thLo);
+        const float b2 = mul_split((m2 - sp * (m2 - (drho - rv2))) - k.h_eps * vF6, k36thHi, k36thLo);
         const float b3 = mul_split(jx + Fx, kSixthHi, kSixthLo), b5 = mul_split(jy + Fy, kSixthHi, kSixthLo);
-        const float b4 = ((m4 - sq * (m4 + rho * vx)) - (1.f - 0.5f * sq) * Fx) * (1.f / 12.f);
-        const float b6 = ((m6 - sq * (m6 + rho * vy)) - (1.f - 0.5f * sq) * Fy) * (1.f / 12.f);
-        const float b7 = 0.25f * ((m7 - sn * (m7 - rho * (vx2 - vy2))) + (1.f - 0.5f * sn) * (2.f * (vx * Fx - vy * Fy)));
-        const float b8 = 0.25f * ((m8 - sn * (m8 - rho * vx * vy)) + (1.f - 0.5f * sn) * (vx * Fy + vy * Fx));
+        const float b4 = ((m4 - sq * (m4 + rho * vx)) - k.h_q * Fx) * (1.f / 12.f);
+        const float b6 = ((m6 - sq * (m6 + rho * vy)) - k.h_q * Fy) * (1.f / 12.f);
+        const float b7 = 0.25f * ((m7 - sn * (m7 - rho * (vx2 - vy2))) + k.guo_pre * (2.f * (vx * Fx - vy * Fy)));
+        const float b8 = 0.25f * ((m8 - sn * (m8 - rho * vx * vy)) + k.guo_pre * (vx * Fy + vy * Fx));
         const float ax = b0 - b1 - 2.f * b2;      // common part of e1..e4
         const float dg = b0 + 2.f * b1 + b2;      // common part of e5..e8
         const float px = b3 - 2.f * b4, py = b5 - 2.f * b6;

@@ -71,6 +71,9 @@ lbm::Coef<C> make_coef(const lbm_params& p)
     // tau = 1/omega as hi + lo.
     k.A = C(p.A);
     k.tau_lo = C(0);
+    k.h_e = C(1.0f - 0.5f * float(p.s_e));
+    k.h_eps = C(1.0f - 0.5f * float(p.s_eps));
+    k.h_q = C(1.0f - 0.5f * float(p.s_q));
     if (p.precision != LBM_FP64) {
         float om = float(1.0 / p.tau);
         float gp = float(1.0 - 0.5 * double(om));

@@ -411,12 +411,22 @@ __device__ __forceinline__ bool strip_walk_step(const T* __restrict__ fin, T* __
 
 // One lattice, grid (strips, row chunks).  MINB > 1 asks the compiler to fit
 // MINB CTAs per SM in the register file (at the price of spills if needed).
+// Launched as a programmatic dependent of the previous kernel on the stream
+// (launch_strip_cfg): each CTA first waits until that kernel has completed
+// and its writes are visible (griddepcontrol.wait), so no CTA touches global
+// memory early; it then lets the next step's CTAs be scheduled as soon as
+// SMs free up, which hides the launch gap between consecutive steps.  The
+// dependents are launched only once every CTA of this grid has passed its
+// launch_dependents (or exited), so a waiting dependent CTA never holds an
+// SM that a CTA of this grid has yet to start on.
 template <typename T, typename C, int COLL, int FORC, int NT, int NS, bool CARRY, int MINB, bool HALO1, bool PSEAM>
 __global__ void __launch_bounds__(NT, MINB)
 k_step_strip(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, int nchunks, Coef<C> k,
              unsigned* __restrict__ status, long long first_wait)
 {
     extern __shared__ __align__(128) unsigned char smem[];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (!staged_alignment_ok(smem, fin, fout)) {
         if (threadIdx.x == 0) atomicOr(status, ST_ALIGN);
         return;
@@ -463,9 +473,20 @@ int launch_strip_cfg(const lbm_params* p, const void* fin, void* fout, unsigned*
     int nchunks = std::max(1, (nsm * per_sm) / nstrips);
     nchunks = std::min(nchunks, std::max(1, p->ny / 16));
     const Coef<C> k = make_coef<C>(*p);
-    kern<<<dim3(nstrips, nchunks), NT, smem, s>>>((const T*)fin, (T*)fout, p->nx, p->ny, nchunks, k, status,
-                                                  first_wait);
-    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_E_CUDA;
+    // programmatic dependent launch (see k_step_strip)
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(nstrips, nchunks);
+    lc.blockDim = dim3(NT);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = s;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&lc, kern, (const T*)fin, (T*)fout, p->nx, p->ny, nchunks, k, status,
+                                             first_wait);
+    return e == cudaSuccess && cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_E_CUDA;
 }
 
 template <typename T, typename C, int NT, int NS, bool CARRY = false, int MINB = 1, bool HALO1 = false,

@@ -92,6 +92,21 @@ def test_run_to_steady_isolates_failures_and_converges_the_rest(lbm, tuning):
     assert done == max(steps)
 
 
+def test_observe_marks_flagged_instances_failed(lbm):
+    """Plain steps and an observation, no run to steady state: an instance
+    whose kernels flagged a non-finite or out-of-domain value is reported
+    failed with its code; the others keep running."""
+    inst = [dict(nx=8, ny=64, kind="slab", T_over_Tc=0.85, tau=1.0, A=-0.304, K=1.0, size=16.0, seed=5),
+            dict(side=48, kind="droplet", T_over_Tc=0.5, tau=0.55, A=-0.152, K=1.0, size=12.0, seed=6)]   # unstable
+    with lbm.Batch(inst) as b:
+        b.init()
+        b.step(20000)
+        b.observe()
+        state, code, _, obs = b.results()
+    assert state[1] == lbm.FAILED and code[1] in (lbm.E_NONFINITE, lbm.E_EOS_DOMAIN)
+    assert state[0] == lbm.RUNNING and code[0] == 0 and np.isfinite(obs["rho_row_mid"][0])
+
+
 def test_coexistence_criterion_stops_when_probes_settle(lbm):
     """tol_coex: both coexistence probes (centre/corner, or mid/edge row) stop
     changing; the final probes match a much longer run."""
