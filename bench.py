@@ -45,7 +45,7 @@ SEED = 20141217 + 2 * 1000
 # taken from, the kernel configuration id and the lattice side; when any of
 # them changes the entry no longer matches and traffic is null.
 TRAFFIC_CAPTURES: dict = {
-    ("ca9aea252e4fa9bd", 10, 4096): (604.12e6 + 546.69e6),
+    ("a98e13cdc4a7b4d3", 10, 4096): (604.09e6 + 546.86e6),
 }
 # Sources of the block-strip step kernel (its configuration table included).
 KERNEL_SOURCES = ["paper_1412_5170_gb300/csrc/lbm_strip.cuh", "paper_1412_5170_gb300/csrc/lbm_strip_f32.cu",
@@ -589,7 +589,8 @@ def run_batch(args):
                       "node_steps_per_s": node_steps / wall},
         "config": {"workload": "batched sweep, %d instances: side U{64..512}, T/Tc U[.5,.9], tau U[.55,1.2], "
                                "K U[1/16,1], R U[10, side/4], droplet or slab; MRT+Guo, A=%g, FP32 deviations; "
-                               "criterion: coexistence probes change < %g per 1000 steps" % (args.batch_n, args.ws_A, args.ws_tol)},
+                               "criterion: coexistence probes change < %g per 1000 steps (rule: %s)"
+                               % (args.batch_n, args.ws_A, args.ws_tol, args.ws_rule)},
     }
     print(json.dumps(line), flush=True)
 
@@ -716,11 +717,9 @@ def _solution(fn, *a):
 # on one launch of the autotuned kernel
 # (sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on.sum / nodes),
 # keyed like TRAFFIC_CAPTURES (sha256 of the kernel sources, configuration
-# id, lattice side); unknown otherwise.  (Counted before the strip kernel's
-# dependent launch and the FP32 MRT's precomputed factors, which leave the
-# FP64 generic kernel's code as it was.)
+# id, lattice side); unknown otherwise.
 FP64_INST_CAPTURES: dict = {
-    ("ca9aea252e4fa9bd", 0, 1024): {"dfma": 73662464 / 1048576, "dadd": 87670784 / 1048576,
+    ("a98e13cdc4a7b4d3", 0, 1024): {"dfma": 73662464 / 1048576, "dadd": 87670784 / 1048576,
                                     "dmul": 40845312 / 1048576},
 }
 
