@@ -214,11 +214,22 @@ __device__ __forceinline__ void force(const Stencil<C>& q, const Coef<C>& k, C& 
 // Moments of the deviations (Eq. 3): drho = sum g (rho = rho_ref + drho),
 // j = sum g e (the w_a rho_ref shift has zero first moment).
 template <typename C>
+__device__ __forceinline__ void momentum(const C g[9], C& jx, C& jy)
+{
+    jx = (g[1] - g[3]) + ((g[5] - g[7]) + (g[8] - g[6]));
+    jy = (g[2] - g[4]) + ((g[5] - g[7]) + (g[6] - g[8]));
+}
+template <typename C>
 __device__ __forceinline__ void moments(const C g[9], C& drho, C& jx, C& jy)
 {
     drho = ((g[0] + (g[1] + g[3])) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]));
-    jx = (g[1] - g[3]) + ((g[5] - g[7]) + (g[8] - g[6]));
-    jy = (g[2] - g[4]) + ((g[5] - g[7]) + (g[6] - g[8]));
+    momentum(g, jx, jy);
+}
+// Sum of the eight moving deviations, the tree the FP32 step's density and
+// mass closure share.
+__device__ __forceinline__ float moving_sum(const float g[9])
+{
+    return ((g[1] + g[3]) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]));
 }
 
 // Deviation equilibrium (Eq. 2 minus w_a rho_ref):
@@ -244,10 +255,14 @@ template <int COLL, int FORC>
 __device__ __forceinline__ void collide_f32(float g[9], float Fx, float Fy, const Coef<float>& k, float& vx,
                                             float& vy, float& rho_out, float psi)
 {
-    float drho, jx, jy;
-    moments(g, drho, jx, jy);
+    // density: the rest deviation plus the moving ones' sum, which the mass
+    // closure at the end reuses (sum9, the psi pass's density, adds in the
+    // same order in FP32)
     const float g0_old = g[0];
-    const float s_old = ((g[1] + g[3]) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]));
+    const float s_old = moving_sum(g);
+    const float drho = g0_old + s_old;
+    float jx, jy;
+    momentum(g, jx, jy);
     const float rho = k.rho_ref + drho;
     const float inv_rho = rcp_nr(rho);
     const float ux = jx * inv_rho, uy = jy * inv_rho;
@@ -358,7 +373,7 @@ __device__ __forceinline__ void collide_f32(float g[9], float Fx, float Fy, cons
     // region: a flat FP32 slab of 8 x 127 nodes then gained mass at 1.6e-4
     // of itself per 8e4 steps and its vapour density drifted by 2e-4 (7e-6
     // and 3e-5 with this form; both measured on the host copy of this code).
-    g[0] = g0_old + (s_old - (((g[1] + g[3]) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]))));
+    g[0] = g0_old + (s_old - moving_sum(g));
 }
 
 // FP64 collision (the compute type C is double), every scheme.

@@ -52,7 +52,10 @@ __device__ __forceinline__ void pull_node(const T* __restrict__ f, int x, int y,
 template <typename C>
 __device__ __forceinline__ C sum9(const C g[9])
 {
-    return ((g[0] + (g[1] + g[3])) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]));
+    if constexpr (sizeof(C) == sizeof(float))
+        return g[0] + moving_sum(g);   // the FP32 collision's density, same order
+    else
+        return ((g[0] + (g[1] + g[3])) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]));
 }
 
 __device__ __forceinline__ void flag_status(unsigned bad, unsigned* status)
