@@ -361,14 +361,17 @@ int lbm_batch_run_to_steady(lbm_batch *b, double tol_v, double tol_rho, double t
  * tol_coex (a stopping rule of the measurement; the paper fixes none):
  *   LBM_COEX_CHANGE  the relative change of each probe since the previous
  *                    check (the default);
- *   LBM_COEX_TAIL    also the estimated change still to come: the probe's
- *                    last two changes d and d' taken as a geometric series of
- *                    ratio r = d/d' (Aitken's extrapolation) give |d| r/(1-r)
- *                    for 0 <= r < 1 and |d| for r < 0; while the changes do
- *                    not shrink (r >= 1), or before three checks, the
- *                    instance does not stop.  A run that creeps towards its
- *                    steady state by small, slowly shrinking changes then
- *                    runs on until what is left is below the tolerance.
+ *   LBM_COEX_TAIL    also the estimated change still to come: two
+ *                    successive changes d and d' of a probe taken as a
+ *                    geometric series of ratio r = d/d' (Aitken's
+ *                    extrapolation) give |d| r/(1-r) for 0 <= r < 1 and |d|
+ *                    for r < 0; the estimate from the last pair of changes
+ *                    and from the pair before must both be below the
+ *                    tolerance.  While the changes do not shrink (r >= 1),
+ *                    or before four checks, the instance does not stop.  A
+ *                    run that creeps towards its steady state by small,
+ *                    slowly shrinking changes then runs on until what is
+ *                    left is below the tolerance.
  * Applies from the next check on; LBM_E_INVALID for another value. */
 #define LBM_COEX_CHANGE 0
 #define LBM_COEX_TAIL 1

@@ -229,11 +229,13 @@ __device__ __forceinline__ double coex_tail(double d, double dp)
 // coexistence densities (liquid and vapour probe: centre and corner node of a
 // droplet or bubble, mid and edge row of a slab) changed by less than tol_coex
 // relative since the previous check -- with coex_rule LBM_COEX_TAIL, also
-// their estimated remaining changes (coex_tail) -- (a tolerance <= 0
+// their estimated remaining changes (coex_tail) from the last two pairs of
+// changes -- (a tolerance <= 0
 // disables it), and -- with or without a decision -- as failed when a kernel
 // flagged it.  probe_prev holds
 // each instance's probes at the previous check and their changes then.
-struct ProbeHist { double pl, pv, dl, dv; };   // probes at the previous check and their changes then
+// probes at the previous check, their changes then and the changes before
+struct ProbeHist { double pl, pv, dl, dv, dl2, dv2; };
 
 __global__ void __launch_bounds__(256)
 k_reduce_batch(const BInst* __restrict__ inst, const BPart* __restrict__ parts, int* __restrict__ state,
@@ -292,9 +294,15 @@ k_reduce_batch(const BInst* __restrict__ inst, const BPart* __restrict__ parts, 
         const ProbeHist pp = probe_prev[i];
         const double dl = pl - pp.pl, dv = pv - pp.pv;
         double dcoex = fmax(fabs(dl) / fabs(pl), fabs(dv) / fabs(pv));   // NaN before the first check
-        if (coex_rule == LBM_COEX_TAIL && dcoex == dcoex)
-            dcoex = fmax(dcoex, fmax(coex_tail(dl, pp.dl) / fabs(pl), coex_tail(dv, pp.dv) / fabs(pv)));
-        probe_prev[i] = ProbeHist{pl, pv, dl, dv};
+        if (coex_rule == LBM_COEX_TAIL && dcoex == dcoex) {
+            // the estimate from this check's pair of changes and from the previous pair: both
+            // must be small, so that one change whose sign the rounding noise flipped cannot
+            // pass a slow monotone approach for an alternating one
+            const double tl = fmax(coex_tail(dl, pp.dl), coex_tail(pp.dl, pp.dl2));
+            const double tv = fmax(coex_tail(dv, pp.dv), coex_tail(pp.dv, pp.dv2));
+            dcoex = fmax(dcoex, fmax(tl / fabs(pl), tv / fabs(pv)));
+        }
+        probe_prev[i] = ProbeHist{pl, pv, dl, dv, pp.dl, pp.dv};
         if ((tol_v > 0 && o.max_dv < tol_v) || (tol_rho > 0 && o.max_drho < tol_rho) ||
             (tol_coex > 0 && dcoex < tol_coex))
             state[i] = B_CONVERGED;

@@ -59,14 +59,25 @@ def test_coexistence_tail_refuses_until_the_changes_shrink():
 
 def test_coexistence_measure_takes_the_larger_probe_and_rule():
     """The criterion's quantity: the probes' relative change since the
-    previous check, and with rule "tail" at least their relative tail."""
+    previous check, and with rule "tail" at least their relative tails from
+    this check's pair of changes and from the pair before."""
     b = _bench()
+    nan = float("nan")
+    unknown = ((nan, nan), (nan, nan))
     prev, cur = (0.4, 0.01), (0.4 + 4e-7, 0.01 + 2e-8)
-    m, d = b.coex_measure(prev, cur, (float("nan"), float("nan")), "change")
-    assert d == (cur[0] - prev[0], cur[1] - prev[1])
+    m, hist = b.coex_measure(prev, cur, unknown, "change")
+    d = (cur[0] - prev[0], cur[1] - prev[1])
+    assert hist == ((d[0], nan), (d[1], nan)) or (hist[0][0] == d[0] and hist[1][0] == d[1])
     assert m == max(abs(d[0]) / cur[0], abs(d[1]) / cur[1])
     assert abs(m - 2e-8 / (0.01 + 2e-8)) < 1e-6 * m       # the vapour probe's
-    assert b.coex_measure(prev, cur, (float("nan"), float("nan")), "tail")[0] == float("inf")
-    # vapour probe shrinking by 0.99 per check: its tail is 99 changes
-    m, _ = b.coex_measure(prev, cur, (d[0] / 0.5, d[1] / 0.99), "tail")
-    assert abs(m - 99 * abs(d[1]) / cur[1]) < 1e-9 * m
+    assert b.coex_measure(prev, cur, unknown, "tail")[0] == float("inf")
+    # both probes shrinking geometrically (0.5 and 0.99 per check): the vapour
+    # probe's tail is 99 of its last changes, and 99 of the one before
+    # (100 of the last) from the previous pair, the larger
+    hist = ((d[0] / 0.5, d[0] / 0.25), (d[1] / 0.99, d[1] / 0.99 ** 2))
+    m, _ = b.coex_measure(prev, cur, hist, "tail")
+    assert abs(m - 100 * abs(d[1]) / cur[1]) < 1e-8 * m
+    # one sign flip of the last change does not hide a slow approach before it
+    hist = ((-d[0], -d[0] / 0.5), (-d[1], -d[1] / 0.99))
+    m, _ = b.coex_measure(prev, cur, hist, "tail")
+    assert m >= 99 * abs(d[1]) / cur[1] * 0.99

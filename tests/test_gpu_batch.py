@@ -75,6 +75,12 @@ TUNINGS = [None, (512, 2, 16, True)]
 
 @pytest.mark.parametrize("tuning", TUNINGS)
 def test_run_to_steady_isolates_failures_and_converges_the_rest(lbm, tuning):
+    """One unstable instance fails on its own; the two slabs converge on the
+    coexistence criterion (tail rule).  (The all-node criterion tol_rho is not
+    used here: in FP32 the rounding of the collision's momentum lets a slab
+    drift along y by ~1e-3 lattice units per 10^4 steps, which keeps the
+    densities at its interface nodes changing by 1e-4-1e-3 per check although
+    the coexistence densities have settled.)"""
     inst = [dict(nx=8, ny=64, kind="slab", T_over_Tc=0.85, tau=1.0, A=-0.304, K=1.0, size=16.0, seed=5),
             dict(side=48, kind="droplet", T_over_Tc=0.5, tau=0.55, A=-0.152, K=1.0, size=12.0, seed=6),   # unstable
             dict(nx=12, ny=64, kind="slab", T_over_Tc=0.8, tau=0.9, A=-0.304, K=0.5, size=16.0, seed=7)]
@@ -82,14 +88,23 @@ def test_run_to_steady_isolates_failures_and_converges_the_rest(lbm, tuning):
         if tuning:
             b.set_tuning(*tuning)
         b.init()
-        st, done = b.run_to_steady(tol_rho=1e-6, check_every=500, max_steps=100000)
+        b.set_coex_rule("tail")
+        st, done = b.run_to_steady(tol_coex=1e-6, check_every=500, max_steps=100000)
         state, code, steps, obs = b.results()
     assert st == lbm.OK
     assert state[1] == lbm.FAILED and code[1] in (lbm.E_NONFINITE, lbm.E_EOS_DOMAIN)
     assert state[0] == lbm.CONVERGED and state[2] == lbm.CONVERGED
-    assert obs["max_drho"][0] < 1e-6 and obs["max_drho"][2] < 1e-6
     assert steps[1] < steps[0] or steps[1] < steps[2]
     assert done == max(steps)
+    # the converged slabs' coexistence densities against a much longer run
+    with lbm.Batch([inst[0], inst[2]]) as r:
+        r.init()
+        r.step(int(max(steps)) + 20000)
+        r.observe()
+        _, _, _, ref = r.results()
+    for j, i in ((0, 0), (1, 2)):
+        assert abs(obs["rho_row_mid"][i] / ref["rho_row_mid"][j] - 1) < 1e-5
+        assert abs(obs["rho_row0"][i] / ref["rho_row0"][j] - 1) < 1e-4
 
 
 def test_observe_marks_flagged_instances_failed(lbm):
@@ -140,7 +155,8 @@ def test_tail_rule_decides_as_the_host_rule(lbm):
     """LBM_COEX_TAIL on the device against the host statement of the same
     rule (bench.coex_measure): stepping one check interval at a time, every
     instance stops exactly at the first check where its probes' relative
-    change and estimated remaining change are both below tol_coex, and no
+    change and the remaining changes estimated from the last two pairs of
+    changes are all below tol_coex, and no
     earlier than under the change-only rule; its probes then sit at least as
     close to a much longer run's."""
     bench = _bench()
@@ -153,7 +169,8 @@ def test_tail_rule_decides_as_the_host_rule(lbm):
         b.init()
         b.set_coex_rule("tail")
         prev = [None] * len(inst)
-        dprev = [(float("nan"), float("nan"))] * len(inst)
+        nan = float("nan")
+        hist = [((nan, nan), (nan, nan))] * len(inst)
         expect = [None] * len(inst)
         for k in range(1, 200):
             st, _ = b.run_to_steady(tol_coex=tol, check_every=every, max_steps=every)
@@ -163,7 +180,7 @@ def test_tail_rule_decides_as_the_host_rule(lbm):
                     continue
                 cur = (obs[keys[i][0]][i], obs[keys[i][1]][i])
                 if prev[i] is not None:
-                    m, dprev[i] = bench.coex_measure(prev[i], cur, dprev[i], "tail")
+                    m, hist[i] = bench.coex_measure(prev[i], cur, hist[i], "tail")
                     if m < tol:
                         expect[i] = k * every
                 prev[i] = cur
