@@ -22,9 +22,12 @@ namespace {
 // Observes each chunk row of the walk: per node Eq. 6's force, rho and v,
 // then the optional moment fields (FP64, 128-bit stores), the snapshot
 // compare / store, and the running reductions.  The mass is N rho_ref plus
-// the FP64 sum of the deviations drho (one FP64 add per node: the FP64 pipe
-// is narrow on this GPU); the maxima are taken on |v|^2 and |v - v_snap|^2
-// in the compute type (exact) and rooted once per CTA.
+// the sum of the deviations drho: in FP64 for an FP64 lattice; for FP32
+// deviations a float pair (sum, error) kept by Knuth's TwoSum, which carries
+// every addition's rounding exactly into the error term (six FP32 additions
+// a node instead of a conversion and an addition on this GPU's narrow FP64
+// pipe), converted to FP64 once per thread.  The maxima are taken on |v|^2
+// and |v - v_snap|^2 in the compute type (exact) and rooted once per CTA.
 template <typename T, typename C>
 struct ObsRow {
     int mode, nx, ny;
@@ -35,6 +38,7 @@ struct ObsRow {
     DevStats* __restrict__ ds;
     double dmass, row_mid, row0;
     C mv2, mdv2, dmax, ndmin;
+    float ms = 0.f, me = 0.f;   // FP32: running sum of drho and its accumulated rounding
 
     __device__ __forceinline__ void operator()(int y, int x, bool active, C (&gc)[9][4], const C (&rm)[6],
                                                const C (&r0)[6], const C (&rp)[6], const Coef<C>& k,
@@ -54,7 +58,14 @@ struct ObsRow {
             mv2 = (s2 > mv2 || s2 != s2) ? s2 : mv2;      // NaN wins (reported as huge)
             dmax = d4[j] > dmax ? d4[j] : dmax;
             ndmin = -d4[j] > ndmin ? -d4[j] : ndmin;
-            dmass += double(d4[j]);
+            if constexpr (sizeof(C) == sizeof(float)) {
+                const float t = ms + d4[j];
+                const float bp = t - ms;
+                me += (ms - (t - bp)) + (d4[j] - bp);
+                ms = t;
+            } else {
+                dmass += double(d4[j]);
+            }
         }
         if (!isfinite(dmax) || !isfinite(ndmin) || !isfinite(mv2)) bad |= ST_NONFINITE;
         if (y == ny / 2 || y == 0 || (mode & OBS_FIELDS)) {
@@ -137,6 +148,7 @@ k_observe_strip(const T* __restrict__ fin, int nx, int ny, int nchunks, Coef<C> 
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     // nodes this CTA observed: its rows times its strip's columns
     const double cta_nodes = double(y1 > y0 ? y1 - y0 : 0) * double(min(4 * NT, nx - x0));
+    if constexpr (sizeof(C) == sizeof(float)) row.dmass = double(row.ms) + double(row.me);
     double v[7] = {warp_sum(row.dmass), warp_sum(row.row_mid), warp_sum(row.row0), warp_max_root(row.mv2),
                    warp_max_root(row.mdv2), 0.0, 0.0};
     const C wdmax = warp_max(row.dmax), wndmin = warp_max(row.ndmin);
