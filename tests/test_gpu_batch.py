@@ -377,3 +377,11 @@ def test_batch_li_model_needs_eq4_force(lbm):
     instance has another A is rejected, as a single lattice would be."""
     with pytest.raises(lbm.LbmError):
         lbm.Batch(instances()[:1], collision="bgk", forcing="li", sigma=0.105)
+
+
+def test_coex_rule_rejects_unknown_values(lbm):
+    with lbm.Batch(instances()[:1]) as b:
+        assert lbm.lbm_batch_set_coex_rule(b.h, 2) == lbm.E_INVALID
+        assert lbm.lbm_batch_set_coex_rule(b.h, -1) == lbm.E_INVALID
+        b.set_coex_rule("change")
+        b.set_coex_rule("tail")

@@ -411,3 +411,13 @@ def test_stage_wait_timeout_is_reported_and_the_context_recovers(lbm, precision)
         ref, ost = oracle.run(q, oracle.init_rest(rho0), steps)
         assert ost == oracle.OK
         assert np.abs(f - ref).max() / np.abs(ref).max() < 1e-12
+
+
+def test_fma_peak_measures_both_precisions(lbm):
+    """lbm_fma_peak, the FP64 step's roofline: the FP64 FMA rate is a small
+    fraction of the FP32 one on this GPU, both positive and below what the
+    clock and SM count allow (152 SMs x 2.1 GHz x 128 FP32 lanes x 2 flops =
+    82 TFLOP/s)."""
+    p64, p32 = lbm.fma_peak("fp64"), lbm.fma_peak("fp32")
+    assert 0.1 < p64 < p32 / 8
+    assert 10.0 < p32 < 90.0
