@@ -224,6 +224,20 @@ int lbm_wait_io(lbm_ctx *ctx);
 int lbm_read_populations(lbm_ctx *ctx, double *f_host);
 int lbm_write_populations(lbm_ctx *ctx, const double *f_host);
 
+/* Rows [y0, y0 + nrows) of the stored state -- the post-collision
+ * populations of the previous step, pulled by the next one (Eq. 1) -- copied
+ * out of the lattice into a device buffer the caller owns (to_lattice = 0)
+ * or from it into the lattice (to_lattice = 1).  Buffer layout [9][nrows][nx]
+ * in the storage type: double for LBM_FP64, float deviations f - w rho_ref
+ * for LBM_FP32_DEV.  The copies are queued on the context's stream, in order
+ * with its steps, without synchronising.  This is the y-slab halo exchange
+ * of one lattice split over ranks: a node's update reads the stored rows
+ * within two of it (the pull one row, the psi of Eq. 6's stencil one row
+ * further), so each rank steps its rows plus two halo rows per side and
+ * refreshes those from its neighbours after every step.  LBM_E_INVALID for
+ * rows outside [0, ny) or a null buffer. */
+int lbm_copy_rows(lbm_ctx *ctx, int y0, int nrows, void *buf_dev, int to_lattice);
+
 /* Checkpoint: header (magic, version, params, steps), the raw population
  * buffer and an FNV-1a checksum.  lbm_load needs a context created with the
  * same params; it restores the state bit for bit. */

@@ -570,6 +570,21 @@ int lbm_write_populations(lbm_ctx* c, const double* f_host)
     return reset_state(c);
 }
 
+int lbm_copy_rows(lbm_ctx* c, int y0, int nrows, void* buf_dev, int to_lattice)
+{
+    if (!c || !buf_dev || nrows < 0 || y0 < 0 || (long long)y0 + nrows > c->p.ny) return LBM_E_INVALID;
+    const size_t es = tsize(c->p), n = (size_t)c->p.nx * c->p.ny, rows = (size_t)nrows * c->p.nx;
+    unsigned char* f = static_cast<unsigned char*>(c->f[c->cur]);
+    unsigned char* b = static_cast<unsigned char*>(buf_dev);
+    for (int a = 0; a < 9 && nrows > 0; ++a) {
+        unsigned char* lat = f + es * (a * n + (size_t)y0 * c->p.nx);
+        unsigned char* buf = b + es * (a * rows);
+        LBM_CUDA(cudaMemcpyAsync(to_lattice ? lat : buf, to_lattice ? buf : lat, es * rows, cudaMemcpyDeviceToDevice,
+                                 c->stream));
+    }
+    return LBM_OK;
+}
+
 int lbm_save(lbm_ctx* c, const char* path)
 {
     if (!c || !path) return LBM_E_INVALID;

@@ -105,6 +105,7 @@ _PROTOS = {
     "lbm_wait_io": (ctypes.c_int, [_vp]),
     "lbm_read_populations": (ctypes.c_int, [_vp, _vp]),
     "lbm_write_populations": (ctypes.c_int, [_vp, _vp]),
+    "lbm_copy_rows": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int]),
     "lbm_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
     "lbm_load": (ctypes.c_int, [_vp, ctypes.c_char_p]),
     "lbm_inject_stage_timeout": (ctypes.c_int, [_vp]),
@@ -323,6 +324,16 @@ class Lattice:
         f = np.ascontiguousarray(f, dtype=np.float64)
         assert f.shape == (9,) + self.shape
         check(lbm_write_populations(self.ctx, _host_ptr(f)), "lbm_write_populations")
+
+    def copy_rows(self, y0: int, buf, to_lattice: bool = False):
+        """Stored rows [y0, y0 + buf.shape[1]) to (to_lattice False) or from
+        (True) a contiguous CUDA tensor buf of shape (9, nrows, nx) in the
+        storage type (float64 for FP64, float32 deviations for FP32), queued
+        on the lattice's stream."""
+        assert buf.is_cuda and buf.is_contiguous() and buf.dim() == 3 and buf.shape[0] == 9
+        assert buf.shape[2] == self.shape[1]
+        check(lbm_copy_rows(self.ctx, int(y0), int(buf.shape[1]), _vp(buf.data_ptr()), int(bool(to_lattice))),
+              "lbm_copy_rows")
 
     def save(self, path):
         check(lbm_save(self.ctx, str(path).encode()), "lbm_save")

@@ -19,6 +19,12 @@ tensors; NCCL takes the same calls on device tensors): each rank sends its
 top rows to the rank above and its bottom rows to the rank below, and
 receives its halos from them.  With one rank the halos are its own
 boundary rows (periodic wrap).
+
+exchange_lattice does the same for an extended slab held by the library
+(a Lattice of ny_rank + 2 HALO rows): the rows move between the lattice's
+stored state (the post-collision populations the next step pulls) and
+device buffers by lbm_copy_rows on the lattice's stream, and between
+ranks by the same point-to-point calls on that stream.
 """
 from __future__ import annotations
 
@@ -99,3 +105,33 @@ def gather(ext: np.ndarray, rank: int, world: int, ny: int) -> np.ndarray:
     for r, (y0, y1) in enumerate(spans):
         parts[r] = got[r][:, :y1 - y0, :]
     return torch.cat(parts, dim=1).numpy()
+
+
+def exchange_lattice(lat, rank: int, world: int, bufs=None):
+    """Refresh the halo rows of an extended slab held by a library Lattice
+    (2 HALO of its rows are halo, HALO at each end) from its neighbours'
+    boundary rows of the stored state, after a step.  bufs: four device
+    buffers (9, HALO, nx) of the storage type from an earlier call, or None;
+    returns them for the next call.  Collective over the world's ranks; with
+    one rank the lattice's own rows (periodic wrap)."""
+    import torch
+    ny_ext, nx = lat.shape
+    if bufs is None:
+        dt = torch.float64 if lat.p.precision == 0 else torch.float32
+        bufs = [torch.empty((9, HALO, nx), dtype=dt, device="cuda") for _ in range(4)]
+    top, bottom, lower, upper = bufs
+    lat.copy_rows(ny_ext - 2 * HALO, top)    # the rank above's lower halo
+    lat.copy_rows(HALO, bottom)              # the rank below's upper halo
+    if world == 1:
+        lower, upper = top, bottom
+    else:
+        import torch.distributed as dist
+        up, down = (rank + 1) % world, (rank - 1) % world
+        with torch.cuda.stream(lat.stream):   # ordered with the copies on the lattice's stream
+            reqs = [dist.isend(top, up, tag=1), dist.isend(bottom, down, tag=2),
+                    dist.irecv(lower, down, tag=1), dist.irecv(upper, up, tag=2)]
+            for r in reqs:
+                r.wait()
+    lat.copy_rows(0, lower, to_lattice=True)
+    lat.copy_rows(ny_ext - HALO, upper, to_lattice=True)
+    return bufs
