@@ -567,7 +567,7 @@ def run_batch(args):
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         b.set_coex_rule(args.ws_rule)
-        st, done = b.run_to_steady(tol_coex=args.ws_tol, check_every=1000, max_steps=args.ws_max_steps)
+        st, done = b.run_to_steady(tol_coex=args.batch_tol, check_every=1000, max_steps=args.batch_max_steps)
         wall = time.perf_counter() - t1
         state, code, steps, obs = b.results()
     peak, peak_kind = measured_peaks()
@@ -590,7 +590,7 @@ def run_batch(args):
         "config": {"workload": "batched sweep, %d instances: side U{64..512}, T/Tc U[.5,.9], tau U[.55,1.2], "
                                "K U[1/16,1], R U[10, side/4], droplet or slab; MRT+Guo, A=%g, FP32 deviations; "
                                "criterion: coexistence probes change < %g per 1000 steps (rule: %s)"
-                               % (args.batch_n, args.ws_A, args.ws_tol, args.ws_rule)},
+                               % (args.batch_n, args.ws_A, args.batch_tol, args.ws_rule)},
     }
     print(json.dumps(line), flush=True)
 
@@ -961,8 +961,10 @@ def main():
     ap.add_argument("--ws-epochs", type=int, default=3000)
     ap.add_argument("--ws-fp64", type=int, default=64, help="held-out instances also run on the FP64 path")
     ap.add_argument("--ws-A", type=float, default=-0.84, help="Eq. 6 weight A of the sweep (epsilon = -2A = 1.68)")
-    ap.add_argument("--ws-tol", type=float, default=1e-5, help="coexistence-density change per 1000 steps")
-    ap.add_argument("--ws-max-steps", type=int, default=100000)
+    ap.add_argument("--ws-tol", type=float, default=2e-6, help="coexistence-density change per 1000 steps")
+    ap.add_argument("--ws-max-steps", type=int, default=150000)
+    ap.add_argument("--batch-tol", type=float, default=1e-5, help="--mode batch: coexistence criterion")
+    ap.add_argument("--batch-max-steps", type=int, default=100000)
     ap.add_argument("--ws-rule", default="tail", choices=["change", "tail"],
                     help="coexistence criterion: change per check, or also the estimated change still to come")
     ap.add_argument("--cpu-steps", type=int, default=700,
